@@ -1,0 +1,302 @@
+/*
+ * nnqp.h -- C ABI of the GB300-native non-negative diffusion solver.
+ *
+ * Method: Chang, Karra & Nakshatrala, "An optimization-based framework for
+ * ... non-negative ... anisotropic diffusion" (arXiv 1506.08435).
+ *   - The Galerkin P1 discretisation of -div(D grad c) = f with Dirichlet
+ *     data c^p on Gamma^D and zero-flux Neumann data elsewhere (Sec. 2.1.2,
+ *     Sec. 2.1.3) gives K c = f with K symmetric positive definite.
+ *   - The non-negative methodology replaces K c = f by the convex QP
+ *       minimize 1/2 <c; K c> - <c; f>  subject to  lo <= c <= hi
+ *     (Sec. 2.1.4 with lo = 0; Sec. 2.2.2 with c_min, c_max; Sec. 5 remark:
+ *     the upper bound 1 is enforced as well).
+ *   - Transient problems use backward Euler with the capacity matrix M:
+ *       Kt = M/dt + K,  ft^(n+1) = f + M c^(n)/dt   (Sec. 2.2.2; the printed
+ *     formula has c^(n+1) in ft, which is read as c^(n)),
+ *     and the Jacobian (Kt) is assembled once (Sec. 3.2).
+ *   - Dispersion tensor D = (a_T |v| + D_M) I + (a_L - a_T) v v^T / |v|
+ *     from a cell-wise velocity (Sec. 5; Algorithm 1 takes the cell-wise
+ *     velocity as input).
+ *
+ * Conventions for every entry point:
+ *   - Return value: NN_OK or an nn_status error; nn_last_error() gives a
+ *     thread-local message for the last failing call on this thread.
+ *   - Streams are CUDA streams (cudaStream_t) passed as void*; NULL is the
+ *     legacy default stream.  Calls are ordered on that stream; a call that
+ *     returns results to host memory synchronizes that stream.
+ *   - Memory flags (NN_MEM_HOST / NN_MEM_DEVICE) say where caller arrays
+ *     live.  Caller arrays are borrowed for the duration of the call only;
+ *     the library copies what it keeps.
+ *   - Handles (nn_system, nn_server) are owned by the library and released
+ *     with the matching *_destroy call.
+ *   - Floating point is IEEE double unless stated; index arrays are int32
+ *     (node and element ids < 2^31).
+ *   - Invalid input is rejected on the host or by a device-side check that
+ *     writes a status word; no entry point traps or asserts on the device.
+ */
+#ifndef NNQP_H
+#define NNQP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    NN_OK = 0,
+    NN_ERR_INVALID_ARG = 1,    /* bad sizes, pointers, flags, connectivity */
+    NN_ERR_INFEASIBLE = 2,     /* lo > hi, or a Dirichlet value outside [lo, hi] */
+    NN_ERR_NOT_SPD = 3,        /* an element tensor D_e is not symmetric positive definite */
+    NN_ERR_OOM = 4,            /* device allocation failed */
+    NN_ERR_NOT_CONVERGED = 5,  /* iteration cap reached; best feasible iterate returned */
+    NN_ERR_NUMERIC = 6,        /* NaN/Inf met in a reduction or in the input */
+    NN_ERR_TIMEOUT = 7,        /* a bounded device wait gave up */
+    NN_ERR_CUDA = 8,           /* a CUDA runtime call failed */
+    NN_ERR_BUSY = 9,           /* serving: over budget and queue full / result not ready */
+    NN_ERR_DEGENERATE = 10     /* an element has zero measure */
+} nn_status;
+
+enum { NN_MEM_HOST = 0, NN_MEM_DEVICE = 1 };
+enum { NN_COEF_TENSOR = 0, NN_COEF_VELOCITY = 1 };
+enum { NN_SOLVER_GPCG = 0, NN_SOLVER_LBFGS = 1 };
+enum { NN_PREC_FP64 = 0, NN_PREC_MIXED = 1 };
+enum { NN_FMT_SELL = 0, NN_FMT_CSR = 1 };
+
+/* Last error message of the calling thread ("" if none). */
+const char *nn_last_error(void);
+/* Library version string. */
+const char *nn_version(void);
+/* Number of CUDA kernels this library has launched in this process (all
+ * devices, all threads); for accounting of device work, never reset. */
+uint64_t nn_kernel_launches(void);
+
+/* ------------------------------------------------------------------ mesh */
+
+/* Node and element counts of the structured P1 mesh of [0,1]^dim with
+ * nx x ny (x nz) cells: 2D (nx+1)(ny+1) nodes, 2 nx ny triangles; 3D
+ * (nx+1)(ny+1)(nz+1) nodes, 6 nx ny nz tetrahedra.  (The paper's P1
+ * simplicial spaces, Sec. 2.1.3; the structured split is this library's
+ * canonical mesh: its meshes are unstructured.)  Errors: INVALID_ARG. */
+nn_status nn_mesh_counts(int dim, int nx, int ny, int nz, int64_t *n_nodes, int64_t *n_elems);
+
+/* Writes the canonical structured mesh into caller DEVICE buffers
+ * coords [n_nodes][dim] (FP64, node (i,j,k) at (i/nx, j/ny, k/nz), id
+ * i + (nx+1)(j + (ny+1)k)) and conn [n_elems][dim+1] (int32):
+ *   2D: square (i,j) -> T0 = (v00, v10, v11), T1 = (v00, v11, v01),
+ *       element id 2(i + nx j) + t;
+ *   3D: hexahedron h = i + nx(j + ny k) -> 6 Kuhn tetrahedra, one per axis
+ *       permutation p in lexicographic order (xyz, xzy, yxz, yzx, zxy, zyx),
+ *       vertices v0, v0+e_p0, v0+e_p0+e_p1, v0+e_p0+e_p1+e_p2, id 6h + p.
+ * Stream-ordered, asynchronous.  Errors: INVALID_ARG, CUDA. */
+nn_status nn_mesh_structured(int dim, int nx, int ny, int nz, double *coords, int32_t *conn, void *stream);
+
+/* --------------------------------------------------------------- problem */
+
+typedef struct {
+    int dim;                        /* 2 or 3 */
+    /* Mesh: either explicit arrays (coords != NULL) or the structured mesh
+     * of nn_mesh_structured generated on the device (coords == NULL). */
+    int64_t n_nodes, n_elems;       /* explicit mesh sizes (ignored if structured) */
+    const double *coords;           /* [n_nodes][dim] */
+    const int32_t *conn;            /* [n_elems][dim+1] */
+    int nx, ny, nz;                 /* structured sizes (used when coords == NULL) */
+    /* Element coefficient (cell-wise data, one value per element). */
+    int coef_kind;                  /* NN_COEF_TENSOR: coef [E][3|6] = upper triangle of D_e
+                                       (2D xx,xy,yy; 3D xx,xy,xz,yy,yz,zz);
+                                       NN_COEF_VELOCITY: coef [E][dim] = v_e, D_e by the
+                                       dispersion law with alpha_L, alpha_T, D_M */
+    const double *coef;
+    double alpha_L, alpha_T, D_M;
+    const double *f_elem;           /* [E] source per element, or NULL for f = 0; the load is
+                                       F_e[a] = f_e |e| / (dim+1) (one-point rule) */
+    const uint8_t *dirichlet_mask;  /* [N] 1 = node on Gamma^D */
+    const double *dirichlet_value;  /* [N] c^p at Dirichlet nodes (other entries ignored) */
+    double lo, hi;                  /* bounds c_min, c_max (hi may be +INF, lo may be -INF) */
+    double dt;                      /* 0: steady; > 0: backward Euler step with capacity M */
+    int memory;                     /* NN_MEM_HOST or NN_MEM_DEVICE for every array above */
+} nn_problem;
+
+typedef struct nn_system nn_system;
+
+typedef struct {
+    int build_csr;                  /* also keep the reduced matrix in CSR (for NN_FMT_CSR) */
+    int build_mixed;                /* also build the FP32-value copy (for NN_PREC_MIXED) */
+    int keep_full;                  /* keep the full-node K, M, F (for nn_system_copy_out) */
+} nn_assemble_opts;
+
+void nn_assemble_opts_default(nn_assemble_opts *o);
+
+/* Assembles the system on the device (paper Sec. 3.2, Algorithm 1: the
+ * Jacobian is computed once):
+ *   CSR pattern of the node graph -> element matrices K_e = |e| G^T D_e G,
+ *   consistent capacity M_e = |e|(1+delta_ab)/((d+1)(d+2)), loads F_e ->
+ *   summed per node in element order (deterministic) -> Dirichlet
+ *   elimination A = Kt_FF, b0 = F_F - K_FD c_D (free unknowns numbered in
+ *   ascending node order) -> SELL-32 (and optional CSR / FP32) copies.
+ * Host-side validation: dim, sizes, lo <= hi, Dirichlet values in [lo, hi]
+ * (INFEASIBLE), NaN in coefficients (NUMERIC).  Device-side validation
+ * (status word): connectivity range (INVALID_ARG), zero-measure element
+ * (DEGENERATE), non-SPD D_e (NOT_SPD).  Synchronizes the stream.
+ * On success *out owns all device data; release with nn_system_destroy. */
+nn_status nn_assemble(const nn_problem *p, const nn_assemble_opts *o, void *stream, nn_system **out);
+
+void nn_system_destroy(nn_system *s);
+
+typedef struct {
+    int dim;
+    int64_t n_nodes, n_elems, n_free;
+    int64_t nnz_full;               /* nonzeros of the full-node K */
+    int64_t nnz_free;               /* nonzeros of A = Kt_FF (diagonal included) */
+    int64_t sell_slices, sell_stored; /* SELL-32 slices and stored off-diagonal slots */
+    double lo, hi, dt;
+    size_t device_bytes;            /* device memory held by the system */
+} nn_system_desc;
+
+nn_status nn_system_describe(const nn_system *s, nn_system_desc *d);
+
+/* Copies one internal array into a caller buffer (for verification):
+ *   0 K rowptr int64[N+1], 1 K col int32[nnz], 2 K val f64[nnz], 3 M val f64[nnz],
+ *   4 F f64[N], 5 free->node int32[NF], 6 A rowptr int64[NF+1], 7 A col int32[nnzF],
+ *   8 A val f64[nnzF], 9 b0 f64[NF], 10 coords f64[N*dim], 11 conn int32[E*(dim+1)].
+ * Full-node arrays (0-4) need keep_full.  bytes must equal the array size.
+ * Synchronizes the stream.  Errors: INVALID_ARG. */
+nn_status nn_system_copy_out(const nn_system *s, int what, void *dst, size_t bytes, int dst_memory, void *stream);
+
+/* ------------------------------------------------------------------ solve */
+
+typedef struct {
+    int solver;          /* NN_SOLVER_GPCG (gradient projection + CG, More & Toraldo) or
+                            NN_SOLVER_LBFGS (projected limited-memory quasi-Newton, BLMVM-like) */
+    int precision;       /* NN_PREC_FP64, or NN_PREC_MIXED: FP32 values/vectors in inner solves,
+                            FP64 residual, refinement and KKT */
+    int format;          /* NN_FMT_SELL or NN_FMT_CSR (FP64 only) */
+    double rtol;         /* stop when kkt_rel <= rtol (default 1e-10) */
+    int64_t max_iter;    /* cap on matrix-vector products (default 200000) */
+    int lbfgs_m;         /* L-BFGS memory (default 5, at most 16) */
+    int grid_blocks;     /* persistent grid size; 0 = chosen from the size */
+    double wait_timeout_s; /* bound on every device-side wait (default 5 s) */
+    double inner_rtol;   /* mixed: relative tolerance of each inner solve (default 1e-4) */
+} nn_solve_opts;
+
+void nn_solve_opts_default(nn_solve_opts *o);
+
+typedef struct {
+    int status;          /* nn_status of the solve */
+    int64_t iterations;  /* outer iterations (GPCG phases or L-BFGS steps) */
+    int64_t spmv;        /* matrix-vector products (all precisions) */
+    int64_t spmv64;      /* of which FP64 */
+    int64_t cg_iters;    /* CG iterations (GPCG) */
+    int64_t refinements; /* mixed precision outer steps */
+    double kkt_rel;      /* ||gP||_2 / ||b||_2 at exit (FP64) */
+    double kkt_inf;      /* ||gP||_inf / ||b||_inf */
+    double objective;    /* 1/2 x'Ax - b'x */
+    double time_ms;      /* device time of the call (CUDA events) */
+    double bytes_algo;   /* algorithmic bytes moved (perfect-cache model) */
+    int64_t active_lo, active_hi; /* entries exactly at lo / hi */
+} nn_solve_info;
+
+/* Solves the steady QP  min 1/2 x'Ax - x'b0, lo <= x <= hi  over the free
+ * unknowns (Sec. 2.1.4).  c [N] (full node vector, memory c_memory):
+ * in = warm start (free entries; projected onto the box), out = solution
+ * with Dirichlet entries = c^p.  All iterations run on the device in one
+ * persistent launch.  Bounds are exact on output.  Returns NOT_CONVERGED
+ * (best feasible iterate in c) if max_iter is reached, TIMEOUT if a device
+ * wait gave up.  Synchronizes the stream.  For a transient system
+ * (dt > 0) use nn_step / nn_transient. */
+nn_status nn_qp_solve(nn_system *s, const nn_solve_opts *o, double *c, int c_memory, void *stream,
+                      nn_solve_info *info);
+
+/* One backward-Euler step (Sec. 2.2.2): solves the QP with
+ * b = b0 + M_FF c_prev_F / dt (the c^(n) reading of ft), warm-started from
+ * c_prev; writes c_next [N].  c_prev may equal c_next. */
+nn_status nn_step(nn_system *s, const double *c_prev, double *c_next, int memory, const nn_solve_opts *o,
+                  void *stream, nn_solve_info *info);
+
+/* nsteps backward-Euler steps from c0 in ONE device launch; writes the
+ * final state to c_final [N] and, if c_hist != NULL, every state to
+ * c_hist [nsteps][N].  infos: NULL or [nsteps] per-step records (time_ms
+ * is reported on the first record only). */
+nn_status nn_transient(nn_system *s, const double *c0, int nsteps, double *c_final, double *c_hist, int memory,
+                       const nn_solve_opts *o, void *stream, nn_solve_info *infos);
+
+/* FP64 KKT measures of c (full node vector) for the system's QP; for a
+ * transient system c_prev selects the step's right-hand side (NULL for
+ * steady).  out[0] kkt_rel = ||gP||_2/||b||_2, out[1] ||gP||_inf/||b||_inf,
+ * out[2] 1.0 if lo <= c_F <= hi exactly, out[3] objective.  If b = 0 the
+ * denominators are ||A||_inf * max(|lo|, |hi| finite, 1).  Synchronizes. */
+nn_status nn_kkt_residual(const nn_system *s, const double *c, const double *c_prev, int memory,
+                          double out[4], void *stream);
+
+/* y = A x on the free unknowns (x, y device [NF]); format NN_FMT_SELL or
+ * NN_FMT_CSR; precision NN_PREC_FP64, or NN_PREC_MIXED for the FP32-value
+ * operator (x, y still FP64).  Stream-ordered, asynchronous. */
+nn_status nn_spmv(const nn_system *s, const double *x, double *y, int format, int precision, void *stream);
+
+/* --------------------------------------------------------------- batching */
+
+/* Solves `count` independent steady systems in ONE persistent launch: one
+ * thread block per system, systems taken largest first from a device work
+ * counter, block shape chosen by the autotuner (nn_batch_autotune) or the
+ * default.  c[i] is the full node vector of system i (device memory).
+ * infos: NULL or [count].  Mixed precision uses FP32 inner solves with FP64
+ * refinement per system.  Synchronizes. */
+nn_status nn_batch_solve(int count, nn_system *const *systems, double *const *c, const nn_solve_opts *o,
+                         void *stream, nn_solve_info *infos);
+
+/* Times candidate block shapes (threads per block) on a sample of the
+ * batch for a few iterations and keeps the fastest for later
+ * nn_batch_solve calls in this process; *best_threads receives it. */
+nn_status nn_batch_autotune(int count, nn_system *const *systems, const nn_solve_opts *o, void *stream,
+                            int *best_threads);
+
+/* ---------------------------------------------------------------- serving */
+
+typedef struct nn_server nn_server;
+
+typedef struct {
+    int max_inflight;       /* concurrent requests on the device (default 8) */
+    int queue_capacity;     /* waiting requests before submit returns BUSY (default 100000) */
+    int sm_share_blocks;    /* persistent blocks granted per large request (0 = auto) */
+    nn_solve_opts solve;    /* per-request solver options */
+} nn_serve_opts;
+
+typedef struct {
+    int64_t submitted, completed, failed, rejected;
+    double p50_ms, p99_ms, mean_ms;  /* latency submit -> result ready */
+    double solves_per_s;             /* completed / (last completion - first submit) */
+    size_t bytes_resident, bytes_peak, budget;
+    int64_t inflight_peak;
+} nn_serve_stats_t;
+
+void nn_serve_opts_default(nn_serve_opts *o);
+
+/* Starts a serving loop on the current device: a host scheduler thread
+ * admits queued requests while resident device bytes stay within
+ * hbm_budget_bytes and fewer than max_inflight run; each admitted request
+ * is assembled and solved on its own stream, so solves of different
+ * requests overlap on the device. */
+nn_status nn_serve_create(size_t hbm_budget_bytes, const nn_serve_opts *o, nn_server **out);
+
+/* Queues a steady problem (host arrays, copied before return).  Returns
+ * BUSY if the queue is full, INVALID_ARG/INFEASIBLE for invalid problems,
+ * or INVALID_ARG if the problem alone exceeds the budget. */
+nn_status nn_serve_submit(nn_server *sv, const nn_problem *p, uint64_t *request_id);
+
+/* NN_OK and the solution in c_out [N] (host) once request id finished
+ * (the request is then released); BUSY while queued or running; the
+ * request's failure status if it failed. */
+nn_status nn_serve_poll(nn_server *sv, uint64_t id, double *c_out, nn_solve_info *info);
+
+/* Blocks until every submitted request has finished. */
+nn_status nn_serve_drain(nn_server *sv);
+
+nn_status nn_serve_stats(nn_server *sv, nn_serve_stats_t *st);
+
+void nn_serve_destroy(nn_server *sv);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NNQP_H */

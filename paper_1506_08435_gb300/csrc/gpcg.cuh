@@ -1,0 +1,270 @@
+// Gradient projection + conjugate gradient (GPCG) for the box QP
+//     minimize q(x) = 1/2 x'Ax - b'x   subject to  l <= x <= h
+// (the non-negative formulation, Sec. 2.1.4, and its transient form with
+// c_min, c_max, Sec. 2.2.2; GPCG is the TAO method named in Sec. 3.1).
+// Algorithm after More & Toraldo (SIAM J. Optim. 1, 1991):
+//   * gradient-projection phase: steepest descent along -gP with the Cauchy
+//     step length, projected onto the box, backtracking until the Armijo
+//     condition q(w) - q(x) <= mu g'(w - x) holds; repeated until the
+//     active set stops changing or the decrease stalls (eta1);
+//   * CG phase: Jacobi-preconditioned CG on the face {l < x < h} with the
+//     active entries frozen, stopped when the face residual is small, a
+//     bound is crossed, or the decrease per iteration stalls (eta2); then a
+//     projected search along the CG step.  If every active entry is
+//     binding (its projected gradient is zero) the next phase is CG on the
+//     new face, else gradient projection.
+// Objective differences use q(w) - q(x) = 1/2 (g(x) + g(w))'(w - x), exact
+// for a quadratic, so no large objective values are subtracted.
+//
+// Every vector pass is over the rows owned by the calling thread (Rows);
+// passes are separated by team barriers; every scalar comes out of a team
+// reduction, so all threads take the same branches.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include "team.cuh"
+#include "ops.cuh"
+
+namespace nnqp {
+
+enum : int {
+    ST_OK = 0,
+    ST_NOT_CONVERGED = 5,
+    ST_NUMERIC = 6,
+    ST_TIMEOUT = 7,
+};
+
+template <typename V>
+struct Bounds {
+    double lo, hi;
+    const V *lov;                 // per-entry bounds when non-null
+    const V *hiv;
+    __device__ __forceinline__ V l(int64_t i) const { return lov ? lov[i] : (V)lo; }
+    __device__ __forceinline__ V h(int64_t i) const { return hiv ? hiv[i] : (V)hi; }
+};
+
+template <typename V>
+__device__ __forceinline__ V clampv(V x, V l, V h) {
+    return x < l ? l : (x > h ? h : x);
+}
+
+// Projected gradient of the box QP at x.
+template <typename V>
+__device__ __forceinline__ V proj_grad(V x, V g, V l, V h) {
+    if (x <= l) {
+        if (x >= h) return (V)0;
+        return g < (V)0 ? g : (V)0;
+    }
+    if (x >= h) return g > (V)0 ? g : (V)0;
+    return g;
+}
+
+template <typename V>
+struct GpcgVecs {
+    V *x, *g, *p, *q, *r, *z, *s, *w, *gw;
+    const V *b;
+    const V *dinv;
+};
+
+struct GpcgCtl {
+    double tol;          // stop when ||gP||_2 <= tol
+    double face_tol;     // CG stops when the face residual norm <= face_tol
+    int64_t max_spmv;    // cap on products for this call
+    int gp_max;          // gradient-projection steps per phase
+    int cg_max;          // CG iterations per face
+    double eta1, eta2;   // stall ratios of the GP and CG phases
+    double mu;           // Armijo constant
+};
+
+// vec counts vector streams (one read or write of an n-vector) made by the
+// passes beyond the gathered input and the output of each product; the
+// algorithmic traffic of a call is spmv * B_spmv + vec * n * sizeof(V).
+struct GpcgStats {
+    int64_t spmv = 0, cg = 0, phases = 0, vec = 0;
+    double gp2 = 0.0;
+};
+
+// Runs GPCG from the iterate in v.x (projected first).  On exit v.x holds
+// the final iterate, v.g its gradient (pointers may have been swapped).
+template <class Team, class Op, typename V>
+__device__ int gpcg_solve(Team &T, const Rows &R, const Op &A, const Bounds<V> &B, GpcgVecs<V> &v,
+                          const GpcgCtl &C, GpcgStats &st) {
+    const double tol2 = C.tol * C.tol, ftol2 = C.face_tol * C.face_tol;
+    R.each([&](int64_t i) { v.x[i] = clampv(v.x[i], B.l(i), B.h(i)); });
+    st.vec += 2;
+    if (!T.sync()) return ST_TIMEOUT;
+    {
+        double a[1] = {0.0};
+        A.apply(R, v.x, [&](int64_t i, V ax) {
+            V gi = ax - v.b[i];
+            v.g[i] = gi;
+            V gp = proj_grad(v.x[i], gi, B.l(i), B.h(i));
+            a[0] += (double)gp * (double)gp;
+        });
+        if (!T.reduce(a)) return ST_TIMEOUT;
+        ++st.spmv;
+        st.vec += 1;
+        st.gp2 = a[0];
+    }
+    int status = ST_NOT_CONVERGED;
+    for (;;) {
+        if (!isfinite(st.gp2)) { status = ST_NUMERIC; break; }
+        if (st.gp2 <= tol2) { status = ST_OK; break; }
+        if (st.spmv >= C.max_spmv) break;
+        ++st.phases;
+        // ------------------------------------------------ gradient projection
+        double maxdec = 0.0;
+        for (int it = 0; it < C.gp_max; ++it) {
+            R.each([&](int64_t i) { v.p[i] = -proj_grad(v.x[i], v.g[i], B.l(i), B.h(i)); });
+            st.vec += 3;
+            if (!T.sync()) return ST_TIMEOUT;
+            double a1[1] = {0.0};
+            A.apply(R, v.p, [&](int64_t i, V ap) { a1[0] += (double)v.p[i] * (double)ap; });
+            if (!T.reduce(a1)) return ST_TIMEOUT;
+            ++st.spmv;
+            if (!(a1[0] > 0.0)) break;
+            double alpha = st.gp2 / a1[0];
+            bool accepted = false;
+            double a2[4];
+            for (int ls = 0; ls < 48 && st.spmv < C.max_spmv; ++ls) {
+                a2[0] = a2[1] = a2[2] = a2[3] = 0.0;
+                const V va = (V)alpha;
+                R.each([&](int64_t i) {
+                    V l = B.l(i), h = B.h(i), xi = v.x[i];
+                    V wi = clampv(xi + va * v.p[i], l, h);
+                    v.w[i] = wi;
+                    a2[0] += (double)v.g[i] * (double)(wi - xi);
+                    a2[1] += ((xi <= l || xi >= h) != (wi <= l || wi >= h)) ? 1.0 : 0.0;
+                });
+                if (!T.sync()) return ST_TIMEOUT;
+                A.apply(R, v.w, [&](int64_t i, V aw) {
+                    V gwi = aw - v.b[i];
+                    v.gw[i] = gwi;
+                    V wi = v.w[i];
+                    a2[2] += (double)(v.g[i] + gwi) * (double)(wi - v.x[i]);
+                    V gp = proj_grad(wi, gwi, B.l(i), B.h(i));
+                    a2[3] += (double)gp * (double)gp;
+                });
+                if (!T.reduce(a2)) return ST_TIMEOUT;
+                ++st.spmv;
+                st.vec += 7;
+                if (0.5 * a2[2] <= C.mu * a2[0]) {
+                    accepted = true;
+                    break;
+                }
+                alpha *= 0.5;
+            }
+            if (!accepted) break;
+            V *t = v.x; v.x = v.w; v.w = t;
+            t = v.g; v.g = v.gw; v.gw = t;
+            st.gp2 = a2[3];
+            double dec = -0.5 * a2[2];
+            if (dec > maxdec) maxdec = dec;
+            if (st.gp2 <= tol2 || st.spmv >= C.max_spmv) break;
+            if (a2[1] == 0.0 || dec <= C.eta1 * maxdec) break;
+        }
+        if (st.gp2 <= tol2 || st.spmv >= C.max_spmv || !isfinite(st.gp2)) continue;
+        // ------------------------------------------------ CG on faces
+        for (;;) {
+            double a3[1] = {0.0};
+            R.each([&](int64_t i) {
+                V xi = v.x[i];
+                bool fr = xi > B.l(i) && xi < B.h(i);
+                V ri = fr ? -v.g[i] : (V)0;
+                V zi = v.dinv[i] * ri;
+                v.r[i] = ri;
+                v.z[i] = zi;
+                v.p[i] = zi;
+                v.s[i] = (V)0;
+                a3[0] += (double)ri * (double)zi;
+            });
+            if (!T.reduce(a3)) return ST_TIMEOUT;
+            st.vec += 7;
+            double rho = a3[0];
+            if (!(rho > 0.0)) break;
+            double maxdec = 0.0;
+            for (int k = 0; k < C.cg_max; ++k) {
+                double a4[1] = {0.0};
+                A.apply(R, v.p, [&](int64_t i, V ap) {
+                    V xi = v.x[i];
+                    V qi = (xi > B.l(i) && xi < B.h(i)) ? ap : (V)0;
+                    v.q[i] = qi;
+                    a4[0] += (double)v.p[i] * (double)qi;
+                });
+                if (!T.reduce(a4)) return ST_TIMEOUT;
+                ++st.spmv;
+                st.vec += 1;
+                if (!(a4[0] > 0.0)) break;
+                const double alpha = rho / a4[0];
+                const V va = (V)alpha;
+                double a5[3] = {0.0, 0.0, 0.0};
+                R.each([&](int64_t i) {
+                    V si = v.s[i] + va * v.p[i];
+                    V ri = v.r[i] - va * v.q[i];
+                    V zi = v.dinv[i] * ri;
+                    v.s[i] = si;
+                    v.r[i] = ri;
+                    v.z[i] = zi;
+                    a5[0] += (double)ri * (double)zi;
+                    a5[1] += (double)ri * (double)ri;
+                    V xs = v.x[i] + si;
+                    a5[2] += (xs < B.l(i) || xs > B.h(i)) ? 1.0 : 0.0;
+                });
+                if (!T.reduce(a5)) return ST_TIMEOUT;
+                ++st.cg;
+                st.vec += 9;
+                const double dec = 0.5 * alpha * rho;
+                if (dec > maxdec) maxdec = dec;
+                if (a5[2] > 0.0 || dec <= C.eta2 * maxdec || a5[1] <= ftol2 || st.spmv >= C.max_spmv ||
+                    !(a5[0] > 0.0))
+                    break;
+                const V vb = (V)(a5[0] / rho);
+                rho = a5[0];
+                R.each([&](int64_t i) { v.p[i] = v.z[i] + vb * v.p[i]; });
+                st.vec += 3;
+                if (!T.sync()) return ST_TIMEOUT;
+            }
+            // projected search along the CG step s
+            double alpha = 1.0;
+            bool accepted = false;
+            double a6[5];
+            for (int ls = 0; ls < 48; ++ls) {
+                a6[0] = a6[1] = a6[2] = a6[3] = a6[4] = 0.0;
+                const V va = (V)alpha;
+                R.each([&](int64_t i) {
+                    V xi = v.x[i];
+                    V wi = clampv(xi + va * v.s[i], B.l(i), B.h(i));
+                    v.w[i] = wi;
+                    a6[0] += (double)v.g[i] * (double)(wi - xi);
+                });
+                if (!T.sync()) return ST_TIMEOUT;
+                A.apply(R, v.w, [&](int64_t i, V aw) {
+                    V gwi = aw - v.b[i];
+                    v.gw[i] = gwi;
+                    V wi = v.w[i], l = B.l(i), h = B.h(i);
+                    a6[2] += (double)(v.g[i] + gwi) * (double)(wi - v.x[i]);
+                    V gp = proj_grad(wi, gwi, l, h);
+                    a6[3] += (double)gp * (double)gp;
+                    a6[4] += ((wi <= l || wi >= h) && gp != (V)0) ? 1.0 : 0.0;
+                });
+                if (!T.reduce(a6)) return ST_TIMEOUT;
+                ++st.spmv;
+                st.vec += 7;
+                if (0.5 * a6[2] <= C.mu * a6[0]) {
+                    accepted = true;
+                    break;
+                }
+                alpha *= 0.5;
+            }
+            if (!accepted) break;
+            V *t = v.x; v.x = v.w; v.w = t;
+            t = v.g; v.g = v.gw; v.gw = t;
+            st.gp2 = a6[3];
+            if (st.gp2 <= tol2 || st.spmv >= C.max_spmv || !isfinite(st.gp2)) break;
+            if (a6[4] > 0.0) break;  // a non-binding active entry: back to gradient projection
+        }
+    }
+    return status;
+}
+
+}  // namespace nnqp

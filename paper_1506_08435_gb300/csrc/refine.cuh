@@ -1,0 +1,68 @@
+// Mixed-precision iterative refinement for the box QP.
+//
+// Outer loop in FP64:  g = A64 x - b (FP64 product), KKT test on the
+// projected gradient; the correction problem
+//     minimize 1/2 d'A32 d - d'r   subject to  lo - x <= d <= hi - x
+// (r = -g) is solved by GPCG with FP32 values and FP32 vectors; then
+// x <- P(x + d) in FP64, so the bounds stay exact.  FP32 storage cuts the
+// bytes of every inner product to 8 per stored entry (from 12) and keeps the
+// work off the FP64 pipe; accuracy is recovered by the FP64 residual.
+#pragma once
+#include "gpcg.cuh"
+
+namespace nnqp {
+
+struct MixedStats {
+    int64_t spmv64 = 0, spmv32 = 0, cg = 0, phases = 0, refinements = 0, vec64 = 0, vec32 = 0;
+    double gp2 = 0.0;
+};
+
+template <class Team, class Op64, class Op32>
+__device__ int mixed_solve(Team &T, const Rows &R, const Op64 &A, const Op32 &A32, double lo, double hi,
+                           const double *b, double *x, GpcgVecs<float> &v, float *r32, float *l32, float *h32,
+                           double tol, double inner_rtol, int max_ref, int64_t max_spmv, const GpcgCtl &ctl32,
+                           MixedStats &st) {
+    R.each([&](int64_t i) { x[i] = clampv(x[i], lo, hi); });
+    st.vec64 += 2;
+    if (!T.sync()) return ST_TIMEOUT;
+    for (int ref = 0;; ++ref) {
+        double a[1] = {0.0};
+        A.apply(R, x, [&](int64_t i, double ax) {
+            const double xi = x[i];
+            const double gi = ax - b[i];
+            const double gp = proj_grad(xi, gi, lo, hi);
+            a[0] += gp * gp;
+            r32[i] = (float)(-gi);
+            l32[i] = (float)(lo - xi);
+            h32[i] = (float)(hi - xi);
+            v.x[i] = 0.0f;
+        });
+        if (!T.reduce(a)) return ST_TIMEOUT;
+        ++st.spmv64;
+        st.vec64 += 1;
+        st.vec32 += 4;
+        st.gp2 = a[0];
+        if (!isfinite(st.gp2)) return ST_NUMERIC;
+        if (st.gp2 <= tol * tol) return ST_OK;
+        if (ref >= max_ref || st.spmv64 + st.spmv32 >= max_spmv) return ST_NOT_CONVERGED;
+        ++st.refinements;
+        GpcgCtl c = ctl32;
+        c.tol = inner_rtol * sqrt(st.gp2);
+        if (c.tol < 0.25 * tol) c.tol = 0.25 * tol;
+        c.face_tol = 0.5 * c.tol;
+        c.max_spmv = max_spmv - st.spmv64 - st.spmv32;
+        GpcgStats is;
+        Bounds<float> B{0.0, 0.0, l32, h32};
+        int s = gpcg_solve(T, R, A32, B, v, c, is);
+        st.spmv32 += is.spmv;
+        st.cg += is.cg;
+        st.phases += is.phases;
+        if (s == ST_TIMEOUT || s == ST_NUMERIC) return s;
+        R.each([&](int64_t i) { x[i] = clampv(x[i] + (double)v.x[i], lo, hi); });
+        st.vec64 += 2;
+        st.vec32 += 1;
+        if (!T.sync()) return ST_TIMEOUT;
+    }
+}
+
+}  // namespace nnqp

@@ -1,0 +1,519 @@
+// Persistent single-system solves: one cooperative launch runs a whole QP
+// solve (steady), a whole backward-Euler run (transient: one warm-started QP
+// per step, Sec. 2.2.2 and Algorithm 1), or a mixed-precision refinement
+// loop, with no host round trip between iterations.
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <algorithm>
+#include "internal.h"
+#include "gpcg.cuh"
+#include "refine.cuh"
+
+namespace nnqp {
+
+constexpr int kSolveThreads = 256;
+constexpr int kCounters = 12;   // per-step int64 counters written by the kernel
+constexpr int kScalars = 4;     // per-step double results
+
+enum { MODE_STEADY = 0, MODE_TRANSIENT = 1, MODE_MIXED = 2 };
+
+struct GridArgs {
+    int mode;
+    int64_t n, N, nslices;
+    SellF64 A;
+    CsrF64 Acsr;
+    SellF32Diff A32;
+    SellF64 M;
+    double lo, hi, inv_dt;
+    const double *b0;
+    const double *dinv64;
+    const float *dinv32;
+    const int32_t *free_node;
+    const double *c_in;     // full node vector (warm start)
+    double *c_out;          // full node vector (result), free entries written
+    double *c_hist;         // [nsteps][N] or null
+    int nsteps;
+    double *v64[10];        // x g p q r z s w gw b
+    float *v32[12];         // d g p q r z s w gw r32 l32 h32
+    GpcgCtl ctl;
+    double rtol, den_fallback, b0norm, inner_rtol;
+    int max_ref;
+    GridBarrier *bar;
+    double *partials;
+    unsigned long long timeout_ns;
+    int bar_extra;          // arrivals the barrier waits for beyond the grid (0; 1 only in the stall test)
+    int64_t *counters;      // [nsteps][kCounters]
+    double *scalars;        // [nsteps][kScalars]
+};
+
+template <int FMT>
+__global__ void __launch_bounds__(kSolveThreads) k_solve_grid(GridArgs a) {
+    __shared__ RedSmem sm;
+    GridTeam T{a.bar, a.partials, (int)gridDim.x + a.bar_extra, a.timeout_ns, 0, 0, &sm};
+    const Rows R = rows_of_block(a.n, a.nslices, blockIdx.x, gridDim.x);
+    double *x = a.v64[0];
+    R.each([&](int64_t i) { x[i] = a.c_in[a.free_node[i]]; });
+    if (!T.sync()) return;
+    const int nsteps = a.mode == MODE_TRANSIENT ? a.nsteps : 1;
+    for (int step = 0; step < nsteps; ++step) {
+        int status = ST_OK;
+        int64_t cnt[kCounters] = {0};
+        double den = a.b0norm, gp2 = 0.0;
+        const double *b = a.b0;
+        if (a.mode == MODE_TRANSIENT) {
+            double *bt = a.v64[9];
+            double acc[1] = {0.0};
+            a.M.apply(R, x, [&](int64_t i, double mx) {
+                const double bi = a.b0[i] + mx * a.inv_dt;
+                bt[i] = bi;
+                acc[0] += bi * bi;
+            });
+            if (!T.reduce(acc)) return;
+            den = sqrt(acc[0]);
+            b = bt;
+            cnt[1] += 1;   // products with M (FP64)
+        }
+        if (!(den > 0.0)) den = a.den_fallback;
+        if (a.mode == MODE_MIXED) {
+            GpcgVecs<float> v{a.v32[0], a.v32[1], a.v32[2], a.v32[3], a.v32[4], a.v32[5],
+                              a.v32[6], a.v32[7], a.v32[8], a.v32[9], a.dinv32};
+            MixedStats ms;
+            status = mixed_solve(T, R, a.A, a.A32, a.lo, a.hi, b, x, v, a.v32[9], a.v32[10], a.v32[11],
+                                 a.rtol * den, a.inner_rtol, a.max_ref, a.ctl.max_spmv, a.ctl, ms);
+            if (status == ST_TIMEOUT) return;
+            cnt[1] += ms.spmv64;
+            cnt[2] += ms.spmv32;
+            cnt[3] = ms.cg;
+            cnt[4] = ms.phases;
+            cnt[5] = ms.refinements;
+            cnt[6] = ms.vec64;
+            cnt[7] = ms.vec32;
+            gp2 = ms.gp2;
+        } else {
+            GpcgVecs<double> v{x, a.v64[1], a.v64[2], a.v64[3], a.v64[4], a.v64[5],
+                               a.v64[6], a.v64[7], a.v64[8], b, a.dinv64};
+            GpcgCtl c = a.ctl;
+            c.tol = a.rtol * den;
+            c.face_tol = 0.5 * c.tol;
+            GpcgStats gs;
+            if (FMT == 0) status = gpcg_solve(T, R, a.A, Bounds<double>{a.lo, a.hi, nullptr, nullptr}, v, c, gs);
+            else status = gpcg_solve(T, R, a.Acsr, Bounds<double>{a.lo, a.hi, nullptr, nullptr}, v, c, gs);
+            if (status == ST_TIMEOUT) return;
+            x = v.x;
+            // keep the solution in slot 0 so that the next step starts there
+            if (x != a.v64[0]) {
+                R.each([&](int64_t i) { a.v64[0][i] = x[i]; });
+                x = a.v64[0];
+                if (!T.sync()) return;
+            }
+            cnt[1] += gs.spmv;
+            cnt[3] = gs.cg;
+            cnt[4] = gs.phases;
+            cnt[6] = gs.vec;
+            gp2 = gs.gp2;
+        }
+        // outputs: scatter to the full vectors, count active entries
+        double acc[2] = {0.0, 0.0};
+        double *hist = a.c_hist ? a.c_hist + (int64_t)step * a.N : nullptr;
+        R.each([&](int64_t i) {
+            const double xi = x[i];
+            const int32_t v = a.free_node[i];
+            if (hist) hist[v] = xi;
+            if (step == nsteps - 1) a.c_out[v] = xi;
+            acc[0] += xi <= a.lo ? 1.0 : 0.0;
+            acc[1] += xi >= a.hi ? 1.0 : 0.0;
+        });
+        if (!T.reduce(acc)) return;
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            cnt[0] = status;
+            cnt[8] = (int64_t)acc[0];
+            cnt[9] = (int64_t)acc[1];
+            for (int k = 0; k < kCounters; ++k) a.counters[(int64_t)step * kCounters + k] = cnt[k];
+            a.scalars[step * kScalars + 0] = gp2;
+            a.scalars[step * kScalars + 1] = den;
+        }
+    }
+}
+
+__global__ void k_fill_dirichlet(int64_t N, const uint8_t *dmask, const double *dval, double *c, int nrep,
+                                 int64_t stride) {
+    int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (v >= N || !dmask[v]) return;
+    for (int r = 0; r < nrep; ++r) c[r * stride + v] = dval[v];
+}
+
+// ------------------------------------------------------------------ KKT (FP64)
+
+// g = A x - b with b = b0 (+ M x_prev / dt); partial sums per block of
+// |gP|^2, max |gP|, |b|^2, max |b|, x'Ax - 2 b'x, infeasible count.
+__global__ void __launch_bounds__(256) k_kkt(SellF64 A, SellF64 M, int transient, double inv_dt,
+                                             const double *b0, const double *x, const double *xprev,
+                                             double lo, double hi, double *part) {
+    __shared__ double sm[8][6];
+    const Rows R = rows_of_block(A.n, A.nslices, blockIdx.x, gridDim.x);
+    double s[6] = {0, 0, 0, 0, 0, 0};
+    A.apply(R, x, [&](int64_t i, double ax) {
+        double bi = b0[i];
+        if (transient) {
+            // (M x_prev)_i computed row-wise (the product is cheap next to the check)
+            const int64_t sl = i >> 5, lane = i & 31;
+            const int64_t base = M.sptr[sl];
+            const int w = (int)((M.sptr[sl + 1] - base) >> 5);
+            double m = M.diag[i] * xprev[i];
+            for (int k = 0; k < w; ++k) m += M.val[base + 32 * k + lane] * xprev[M.col[base + 32 * k + lane]];
+            bi += m * inv_dt;
+        }
+        const double xi = x[i];
+        const double g = ax - bi;
+        const double gp = proj_grad(xi, g, lo, hi);
+        s[0] += gp * gp;
+        s[1] = fmax(s[1], fabs(gp));
+        s[2] += bi * bi;
+        s[3] = fmax(s[3], fabs(bi));
+        s[4] += xi * (ax - 2.0 * bi);
+        s[5] += (xi >= lo && xi <= hi) ? 0.0 : 1.0;
+    });
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        s[0] += __shfl_xor_sync(0xffffffffu, s[0], o);
+        s[1] = fmax(s[1], __shfl_xor_sync(0xffffffffu, s[1], o));
+        s[2] += __shfl_xor_sync(0xffffffffu, s[2], o);
+        s[3] = fmax(s[3], __shfl_xor_sync(0xffffffffu, s[3], o));
+        s[4] += __shfl_xor_sync(0xffffffffu, s[4], o);
+        s[5] += __shfl_xor_sync(0xffffffffu, s[5], o);
+    }
+    if (lane == 0)
+        for (int k = 0; k < 6; ++k) sm[warp][k] = s[k];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t[6] = {0, 0, 0, 0, 0, 0};
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            t[0] += sm[w][0];
+            t[1] = fmax(t[1], sm[w][1]);
+            t[2] += sm[w][2];
+            t[3] = fmax(t[3], sm[w][3]);
+            t[4] += sm[w][4];
+            t[5] += sm[w][5];
+        }
+        for (int k = 0; k < 6; ++k) part[blockIdx.x * 6 + k] = t[k];
+    }
+}
+
+__global__ void k_gather_free(int64_t n, const int32_t *free_node, const double *c, double *x) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) x[i] = c[free_node[i]];
+}
+
+// y = A x as a standalone product (FP64 SELL or CSR, or the FP32 operator).
+__global__ void __launch_bounds__(256) k_spmv64(SellF64 A, const double *x, double *y) {
+    const Rows R = rows_of_block(A.n, A.nslices, blockIdx.x, gridDim.x);
+    A.apply(R, x, [&](int64_t i, double v) { y[i] = v; });
+}
+__global__ void __launch_bounds__(256) k_spmvcsr(CsrF64 A, const double *x, double *y) {
+    const Rows R = rows_of_block(A.n, A.nslices, blockIdx.x, gridDim.x);
+    A.apply(R, x, [&](int64_t i, double v) { y[i] = v; });
+}
+__global__ void k_to_f32(int64_t n, const double *x, float *y) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) y[i] = (float)x[i];
+}
+__global__ void __launch_bounds__(256) k_spmv32(SellF32Diff A, const float *x, double *y) {
+    const Rows R = rows_of_block(A.n, A.nslices, blockIdx.x, gridDim.x);
+    A.apply(R, x, [&](int64_t i, float v) { y[i] = (double)v; });
+}
+
+// ------------------------------------------------------------------ host side
+
+namespace {
+
+SellF64 view64(const nn_system *s) {
+    return SellF64{s->NF, s->A64.nslices, s->A64.sptr, s->A64.col, s->A64.val, s->diag64};
+}
+SellF64 viewM(const nn_system *s) {
+    return SellF64{s->NF, s->M64.nslices, s->M64.sptr, s->M64.col, s->M64.val, s->mdiag64};
+}
+SellF32Diff view32(const nn_system *s) {
+    return SellF32Diff{s->NF, s->A32.nslices, s->A32.sptr, s->A32.col, s->A32.val, s->rsum32};
+}
+CsrF64 viewcsr(const nn_system *s) { return CsrF64{s->NF, s->A64.nslices, s->arow, s->acol, s->aval}; }
+
+double den_fallback(const nn_system *s) {
+    double m = 1.0;
+    if (std::isfinite(s->lo)) m = std::max(m, std::fabs(s->lo));
+    if (std::isfinite(s->hi)) m = std::max(m, std::fabs(s->hi));
+    double d = s->anorm_inf * m;
+    return d > 0 ? d : 1.0;
+}
+
+int device_sms() {
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 1;
+    }
+    return sms;
+}
+
+template <typename K>
+int max_coresident(K kern) {
+    int per = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, kSolveThreads, 0);
+    return std::max(per, 1) * device_sms();
+}
+
+// algorithmic bytes of one product (paper's MatMult model, Sec. 4):
+// nnz (s_v + 4) + 4 (n + 1) + s_x n (x read) + s_x n (y written)
+double bytes_spmv(int64_t nnz, int64_t n, int sv, int sx) {
+    return (double)nnz * (sv + 4) + 4.0 * (n + 1) + 2.0 * sx * n;
+}
+
+struct Scratch {
+    DevArena a;
+    cudaStream_t st;
+    ~Scratch() { a.release(st); }
+};
+
+}  // namespace
+
+void fill_info(const nn_system *s, const int64_t *cnt, const double *sc, int precision, nn_solve_info *info) {
+    std::memset(info, 0, sizeof(*info));
+    info->status = (int)cnt[0];
+    info->spmv64 = cnt[1];
+    info->spmv = cnt[1] + cnt[2];
+    info->cg_iters = cnt[3];
+    info->iterations = cnt[4];
+    info->refinements = cnt[5];
+    info->active_lo = cnt[8];
+    info->active_hi = cnt[9];
+    info->kkt_rel = std::sqrt(sc[0]) / sc[1];
+    info->kkt_inf = NAN;
+    info->objective = NAN;
+    info->bytes_algo = cnt[1] * bytes_spmv(s->nnzF, s->NF, 8, 8) + cnt[2] * bytes_spmv(s->nnzF, s->NF, 4, 4) +
+                       (double)cnt[6] * 8.0 * s->NF + (double)cnt[7] * 4.0 * s->NF;
+    (void)precision;
+}
+
+// Runs the persistent solve kernel.  c_in/c_out/c_hist are device arrays.
+nn_status run_grid(nn_system *s, const nn_solve_opts *o, int mode, int nsteps, const double *c_in, double *c_out,
+                   double *c_hist, cudaStream_t st, nn_solve_info *infos, int ninfos) {
+    const int64_t n = s->NF, N = s->N;
+    const bool mixed = mode == MODE_MIXED;
+    const int fmt = o->format;
+    if (mixed && !s->has_mixed) {
+        set_error("mixed precision needs a system assembled with build_mixed = 1");
+        return NN_ERR_INVALID_ARG;
+    }
+    if (mode == MODE_TRANSIENT && !(s->dt > 0.0)) {
+        set_error("transient solve on a steady system (dt = 0)");
+        return NN_ERR_INVALID_ARG;
+    }
+    if (mode != MODE_TRANSIENT && s->dt > 0.0) {
+        set_error("steady solve on a transient system: use nn_step or nn_transient");
+        return NN_ERR_INVALID_ARG;
+    }
+    if (fmt == NN_FMT_CSR && mixed) {
+        set_error("CSR format is available in FP64 only");
+        return NN_ERR_INVALID_ARG;
+    }
+    Scratch S;
+    S.st = st;
+    GridArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.mode = mode;
+    a.n = n;
+    a.N = N;
+    a.nslices = s->A64.nslices;
+    a.A = view64(s);
+    a.Acsr = viewcsr(s);
+    if (s->has_mixed) a.A32 = view32(s);
+    if (s->dt > 0.0) a.M = viewM(s);
+    a.lo = s->lo;
+    a.hi = s->hi;
+    a.inv_dt = s->dt > 0.0 ? 1.0 / s->dt : 0.0;
+    a.b0 = s->b0;
+    a.dinv64 = s->dinv64;
+    a.dinv32 = s->dinv32;
+    a.free_node = s->free_node;
+    a.c_in = c_in;
+    a.c_out = c_out;
+    a.c_hist = c_hist;
+    a.nsteps = nsteps;
+    for (int k = 0; k < 10; ++k) NN_TRY(S.a.alloc(&a.v64[k], n, st));
+    if (mixed)
+        for (int k = 0; k < 12; ++k) NN_TRY(S.a.alloc(&a.v32[k], n, st));
+    a.ctl.max_spmv = o->max_iter;
+    a.ctl.gp_max = 50;
+    a.ctl.cg_max = 1 << 30;
+    a.ctl.eta1 = 0.1;
+    a.ctl.eta2 = 1e-3;
+    a.ctl.mu = 1e-4;
+    a.rtol = o->rtol;
+    a.den_fallback = den_fallback(s);
+    a.b0norm = s->b0norm;
+    a.inner_rtol = o->inner_rtol;
+    a.max_ref = 200;
+    a.timeout_ns = (unsigned long long)(o->wait_timeout_s * 1e9);
+    // grid
+    void (*kern)(GridArgs) = fmt == NN_FMT_CSR ? k_solve_grid<1> : k_solve_grid<0>;
+    const int maxg = max_coresident(kern);
+    int warps = kSolveThreads / 32;
+    int want = (int)std::min<int64_t>((s->A64.nslices + warps - 1) / warps, (int64_t)maxg);
+    if (o->grid_blocks > 0) want = std::min(o->grid_blocks, maxg);
+    want = std::max(want, 1);
+    // NNQP_TEST_STALL_BARRIER=1 makes the grid barrier wait for one block
+    // that does not exist, so every wait runs into its time limit: the test of
+    // the bounded-wait path (no fault, the kernel returns TIMEOUT).
+    const char *stall = getenv("NNQP_TEST_STALL_BARRIER");
+    a.bar_extra = (stall && stall[0] == '1') ? 1 : 0;
+    NN_TRY(S.a.alloc(&a.bar, 1, st));
+    NN_TRY(S.a.alloc(&a.partials, (size_t)2 * kMaxRed * (want + a.bar_extra), st));
+    NN_TRY(S.a.alloc(&a.counters, (size_t)nsteps * kCounters, st));
+    NN_TRY(S.a.alloc(&a.scalars, (size_t)nsteps * kScalars, st));
+    NN_CUDA_TRY(cudaMemsetAsync(a.bar, 0, sizeof(GridBarrier), st));
+    NN_CUDA_TRY(cudaMemsetAsync(a.counters, 0, sizeof(int64_t) * nsteps * kCounters, st));
+    cudaEvent_t e0, e1;
+    NN_CUDA_TRY(cudaEventCreate(&e0));
+    NN_CUDA_TRY(cudaEventCreate(&e1));
+    cudaEventRecord(e0, st);
+    void *args[] = {&a};
+    cudaError_t le = cudaLaunchCooperativeKernel((void *)kern, dim3(want), dim3(kSolveThreads), args, 0, st);
+    count_launch();
+    if (le != cudaSuccess) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        set_error("cooperative launch of %d blocks failed: %s", want, cudaGetErrorString(le));
+        return NN_ERR_CUDA;
+    }
+    // Dirichlet entries of the outputs
+    (k_fill_dirichlet<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(N, s->dmask, s->dval, c_out, 1, 0), ::nnqp::count_launch());
+    if (c_hist) (k_fill_dirichlet<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(N, s->dmask, s->dval, c_hist, nsteps, N), ::nnqp::count_launch());
+    cudaEventRecord(e1, st);
+    std::vector<int64_t> cnt((size_t)nsteps * kCounters);
+    std::vector<double> sc((size_t)nsteps * kScalars);
+    GridBarrier hb;
+    NN_CUDA_TRY(cudaMemcpyAsync(cnt.data(), a.counters, sizeof(int64_t) * cnt.size(), cudaMemcpyDeviceToHost, st));
+    NN_CUDA_TRY(cudaMemcpyAsync(sc.data(), a.scalars, sizeof(double) * sc.size(), cudaMemcpyDeviceToHost, st));
+    NN_CUDA_TRY(cudaMemcpyAsync(&hb, a.bar, sizeof(hb), cudaMemcpyDeviceToHost, st));
+    NN_CUDA_TRY(cudaStreamSynchronize(st));
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (hb.error) {
+        set_error("a device-side wait gave up after %.3g s (wait #%d)", o->wait_timeout_s, hb.where);
+        return (nn_status)hb.error;
+    }
+    nn_status worst = NN_OK;
+    for (int k = 0; k < nsteps; ++k) {
+        nn_solve_info inf;
+        fill_info(s, &cnt[(size_t)k * kCounters], &sc[(size_t)k * kScalars], mixed, &inf);
+        if (k == 0) inf.time_ms = ms;
+        if (infos && k < ninfos) infos[k] = inf;
+        if (inf.status != NN_OK && worst == NN_OK) worst = (nn_status)inf.status;
+    }
+    if (worst == NN_ERR_NOT_CONVERGED) set_error("iteration cap reached before the KKT tolerance");
+    else if (worst == NN_ERR_NUMERIC) set_error("NaN/Inf met in a reduction");
+    return worst;
+}
+
+nn_status kkt_impl(const nn_system *s, const double *c, const double *c_prev, int memory, double out[4],
+                   cudaStream_t st) {
+    if (s->dt > 0.0 && !c_prev) {
+        set_error("nn_kkt_residual: a transient system needs c_prev");
+        return NN_ERR_INVALID_ARG;
+    }
+    Scratch S;
+    S.st = st;
+    const int64_t n = s->NF, N = s->N;
+    double *cfull, *pfull = nullptr, *x, *xp = nullptr, *part;
+    const int nb = (int)std::min<int64_t>(std::max<int64_t>((s->A64.nslices + 7) / 8, 1), 4096);
+    NN_TRY(S.a.alloc(&x, n, st));
+    NN_TRY(S.a.alloc(&part, (size_t)nb * 6, st));
+    cudaMemcpyKind kind = memory == NN_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    NN_TRY(S.a.alloc(&cfull, N, st));
+    NN_CUDA_TRY(cudaMemcpyAsync(cfull, c, sizeof(double) * N, kind, st));
+    (k_gather_free<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, s->free_node, cfull, x), ::nnqp::count_launch());
+    if (s->dt > 0.0) {
+        NN_TRY(S.a.alloc(&pfull, N, st));
+        NN_TRY(S.a.alloc(&xp, n, st));
+        NN_CUDA_TRY(cudaMemcpyAsync(pfull, c_prev, sizeof(double) * N, kind, st));
+        (k_gather_free<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, s->free_node, pfull, xp), ::nnqp::count_launch());
+    }
+    SellF64 M = s->dt > 0.0 ? viewM(s) : view64(s);
+    (k_kkt<<<nb, 256, 0, st>>>(view64(s), M, s->dt > 0.0, s->dt > 0.0 ? 1.0 / s->dt : 0.0, s->b0, x, xp, s->lo,
+                              s->hi, part), ::nnqp::count_launch());
+    std::vector<double> hp((size_t)nb * 6);
+    NN_CUDA_TRY(cudaMemcpyAsync(hp.data(), part, sizeof(double) * hp.size(), cudaMemcpyDeviceToHost, st));
+    NN_CUDA_TRY(cudaStreamSynchronize(st));
+    double t[6] = {0, 0, 0, 0, 0, 0};
+    for (int b = 0; b < nb; ++b) {
+        t[0] += hp[b * 6 + 0];
+        t[1] = std::max(t[1], hp[b * 6 + 1]);
+        t[2] += hp[b * 6 + 2];
+        t[3] = std::max(t[3], hp[b * 6 + 3]);
+        t[4] += hp[b * 6 + 4];
+        t[5] += hp[b * 6 + 5];
+    }
+    double d2 = std::sqrt(t[2]), di = t[3];
+    if (t[2] == 0.0) d2 = di = den_fallback(s);
+    out[0] = std::sqrt(t[0]) / d2;
+    out[1] = t[1] / di;
+    out[2] = t[5] == 0.0 ? 1.0 : 0.0;
+    out[3] = 0.5 * t[4];
+    return NN_OK;
+}
+
+nn_status spmv_impl(const nn_system *s, const double *x, double *y, int format, int precision, cudaStream_t st) {
+    const int nb = (int)std::max<int64_t>((s->A64.nslices + 7) / 8, 1);
+    if (precision == NN_PREC_MIXED) {
+        if (!s->has_mixed) {
+            set_error("nn_spmv: system has no FP32 copy (build_mixed = 0)");
+            return NN_ERR_INVALID_ARG;
+        }
+        Scratch S;
+        S.st = st;
+        float *x32;
+        NN_TRY(S.a.alloc(&x32, s->NF, st));
+        (k_to_f32<<<(unsigned)((s->NF + 255) / 256), 256, 0, st>>>(s->NF, x, x32), ::nnqp::count_launch());
+        (k_spmv32<<<nb, 256, 0, st>>>(view32(s), x32, y), ::nnqp::count_launch());
+        NN_CUDA_TRY(cudaGetLastError());
+        return NN_OK;
+    }
+    if (format == NN_FMT_CSR) (k_spmvcsr<<<nb, 256, 0, st>>>(viewcsr(s), x, y), ::nnqp::count_launch());
+    else (k_spmv64<<<nb, 256, 0, st>>>(view64(s), x, y), ::nnqp::count_launch());
+    NN_CUDA_TRY(cudaGetLastError());
+    return NN_OK;
+}
+
+// Host or device full vectors in and out of run_grid.
+nn_status solve_entry(nn_system *s, const nn_solve_opts *o, int mode, int nsteps, const double *c_in,
+                      double *c_out, double *c_hist, int memory, cudaStream_t st, nn_solve_info *infos,
+                      int ninfos) {
+    if (memory == NN_MEM_DEVICE) return run_grid(s, o, mode, nsteps, c_in, c_out, c_hist, st, infos, ninfos);
+    Scratch S;
+    S.st = st;
+    double *din, *dout, *dhist = nullptr;
+    NN_TRY(S.a.alloc(&din, s->N, st));
+    NN_TRY(S.a.alloc(&dout, s->N, st));
+    if (c_hist) NN_TRY(S.a.alloc(&dhist, (size_t)s->N * nsteps, st));
+    NN_CUDA_TRY(cudaMemcpyAsync(din, c_in, sizeof(double) * s->N, cudaMemcpyHostToDevice, st));
+    nn_status r = run_grid(s, o, mode, nsteps, din, dout, dhist, st, infos, ninfos);
+    if (r == NN_OK || r == NN_ERR_NOT_CONVERGED || r == NN_ERR_NUMERIC) {
+        NN_CUDA_TRY(cudaMemcpyAsync(c_out, dout, sizeof(double) * s->N, cudaMemcpyDeviceToHost, st));
+        if (c_hist)
+            NN_CUDA_TRY(cudaMemcpyAsync(c_hist, dhist, sizeof(double) * s->N * nsteps, cudaMemcpyDeviceToHost, st));
+        NN_CUDA_TRY(cudaStreamSynchronize(st));
+    }
+    return r;
+}
+
+int mode_for(const nn_system *s, const nn_solve_opts *o) {
+    if (s->dt > 0.0) return MODE_TRANSIENT;
+    return o->precision == NN_PREC_MIXED ? MODE_MIXED : MODE_STEADY;
+}
+
+}  // namespace nnqp

@@ -4,11 +4,11 @@
  * Method: Chang, Karra & Nakshatrala, "An optimization-based framework for
  * ... non-negative ... anisotropic diffusion" (arXiv 1506.08435).
  *   - The Galerkin P1 discretisation of -div(D grad c) = f with Dirichlet
- *     data c^p on Gamma^D and zero-flux Neumann data elsewhere (Sec. 2.1.2,
- *     Sec. 2.1.3) gives K c = f with K symmetric positive definite.
+ *     data c^p on Gamma^D and zero-flux Neumann data elsewhere (Sec. 2.1,
+ *     Sec. 2.1.2) gives K c = f with K symmetric positive definite.
  *   - The non-negative methodology replaces K c = f by the convex QP
  *       minimize 1/2 <c; K c> - <c; f>  subject to  lo <= c <= hi
- *     (Sec. 2.1.4 with lo = 0; Sec. 2.2.2 with c_min, c_max; Sec. 5 remark:
+ *     (Sec. 2.1.3 with lo = 0; Sec. 2.2.2 with c_min, c_max; Sec. 5 remark:
  *     the upper bound 1 is enforced as well).
  *   - Transient problems use backward Euler with the capacity matrix M:
  *       Kt = M/dt + K,  ft^(n+1) = f + M c^(n)/dt   (Sec. 2.2.2; the printed
@@ -198,7 +198,7 @@ typedef struct {
 } nn_solve_info;
 
 /* Solves the steady QP  min 1/2 x'Ax - x'b0, lo <= x <= hi  over the free
- * unknowns (Sec. 2.1.4).  c [N] (full node vector, memory c_memory):
+ * unknowns (Sec. 2.1.3).  c [N] (full node vector, memory c_memory):
  * in = warm start (free entries; projected onto the box), out = solution
  * with Dirichlet entries = c^p.  All iterations run on the device in one
  * persistent launch.  Bounds are exact on output.  Returns NOT_CONVERGED

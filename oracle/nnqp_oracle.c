@@ -13,13 +13,13 @@
  *     and a 6-tetrahedron Kuhn split of each hexahedron (reading, see header
  *     of oracle.py).
  *   - Element stiffness  K_e = |e| G^T D G  (the bilinear form B(w;c), Eq.
- *     for B and L in Sec. 2.1.3; Jacobian with F_{1,1} = D, Sec. 3.2),
+ *     for B and L in Sec. 2.1.2; Jacobian with F_{1,1} = D, Sec. 3.2),
  *     consistent mass M_e (F_{0,0} = 1/dt in the transient pointwise
  *     functions, Sec. 3.2), one-point load F_e = f(x_c)|e|/(d+1).
  *   - Dispersion tensor D = (a_T|v| + D_M) I + (a_L - a_T) v v^T/|v|
  *     (Sec. 5, dispersion tensor equation).
  *   - Box-constrained QP  min 1/2 x^T A x - b^T x,  lo <= x <= hi
- *     (Sec. 2.1.4 non-negative formulation; Sec. 2.2.2 transient QP with
+ *     (Sec. 2.1.3 non-negative formulation; Sec. 2.2.2 transient QP with
  *     c_min <= c <= c_max).  Solved by projected Gauss-Seidel (Cryer's
  *     projected SOR with omega = 1) and by MPRGP (Dostal & Schoeberl 2005),
  *     both published methods, written here from their definitions.

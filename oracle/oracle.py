@@ -14,12 +14,12 @@ What each function follows:
 * ``assemble``         -- K_e = |e| G^T D G and the consistent capacity
   matrix M_e (Sec. 3.2, pointwise Jacobian F_{1,1} = D and transient
   F_{0,0} = 1/dt), load F_e = f(x_c)|e|/(d+1) (one-point rule: reading).
-* ``eliminate``        -- Dirichlet values c^p on Gamma^D (Sec. 2.1.2) taken
+* ``eliminate``        -- Dirichlet values c^p on Gamma^D (Sec. 2.1) taken
   out of the unknowns: A = Kt_FF, b = ft_F - Kt_FD c_D with
   Kt = K + M/dt, ft = f + M c^(n)/dt (Sec. 2.2.2; the printed ft uses
   c^(n+1), read as c^(n)).
 * ``solve_qp``         -- the unique minimiser of 1/2 x'Ax - b'x on the box
-  (Sec. 2.1.4, non-negative formulation; Sec. 2.2.2 with c_min, c_max) by
+  (Sec. 2.1.3, non-negative formulation; Sec. 2.2.2 with c_min, c_max) by
   MPRGP to a tight KKT tolerance, then an active-set polish that solves the
   face system exactly.
 * ``pgs``              -- projected Gauss-Seidel, an independent solver.
@@ -295,7 +295,7 @@ def solve_qp(A, b, lo, hi, x0=None, rtol=1e-12, threads=1, maxit=10_000_000):
 
 
 def galerkin(A, b):
-    """Unconstrained Galerkin solve A x = b (Sec. 2.1.4, K c = f)."""
+    """Unconstrained Galerkin solve A x = b (Sec. 2.1.3, K c = f)."""
     A = A.tocsr()
     if A.shape[0] <= 4000:
         return np.linalg.solve(A.toarray(), b)

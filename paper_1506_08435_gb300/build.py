@@ -11,7 +11,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libnnqp.so")
 OBJ = os.path.join(HERE, "_build")
 
-SOURCES = ["scan.cu", "assemble.cu", "solve.cu", "lbfgs.cu", "batch.cu", "serve.cpp", "stubs.cpp", "capi.cpp"]
+SOURCES = ["scan.cu", "assemble.cu", "solve.cu", "batch.cu", "serve.cpp", "capi.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

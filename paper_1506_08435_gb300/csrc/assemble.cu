@@ -4,13 +4,13 @@
 //   -> node/element incidence (sorted by element id)
 //   -> CSR pattern of the node graph (sorted unique columns per row)
 //   -> element kernel: K_e = |e| G^T D_e G (upper triangle), |e|
-//      (bilinear form B(w;c), Sec. 2.1.3; Jacobian F_{1,1} = D, Sec. 3.2;
+//      (bilinear form B(w;c), Sec. 2.1.2; Jacobian F_{1,1} = D, Sec. 3.2;
 //       D_e from the dispersion law, Sec. 5, when a cell velocity is given)
 //   -> node-centric gather: every row sums its elements' contributions in
 //      ascending element order (deterministic, no floating-point atomics);
 //      M_e = |e|(1 + delta_ab)/((d+1)(d+2)) (capacity matrix, F_{0,0} = 1/dt,
 //      Sec. 3.2) and F_e = f_e |e|/(d+1) in the same pass
-//   -> Dirichlet elimination (Sec. 2.1.2 c = c^p on Gamma^D): free unknowns
+//   -> Dirichlet elimination (Sec. 2.1, c = c^p on Gamma^D): free unknowns
 //      in ascending node order, A = K_FF + M_FF/dt, b0 = F_F - K_FD c_D
 //   -> SELL-32 copies (FP64 off-diagonals + diagonal, FP32 off-diagonals +
 //      row sums for the mixed path, M_FF off-diagonals for transients).

@@ -32,8 +32,6 @@ nn_status kkt_impl(const nn_system *s, const double *c, const double *c_prev, in
                    cudaStream_t st);
 nn_status spmv_impl(const nn_system *s, const double *x, double *y, int format, int precision, cudaStream_t st);
 nn_status check_opts(const nn_solve_opts *o);
-nn_status lbfgs_entry(nn_system *s, const nn_solve_opts *o, int nsteps, const double *c_in, double *c_out,
-                      double *c_hist, int memory, cudaStream_t st, nn_solve_info *infos, int ninfos);
 
 nn_status check_opts(const nn_solve_opts *o) {
     if (!o) {
@@ -221,9 +219,6 @@ static nn_status solve_common(nn_system *s, const nn_solve_opts *o, int want_tra
     if (!want_transient && s->dt > 0.0) {
         set_error("this system is transient (dt > 0): use nn_step or nn_transient");
         return NN_ERR_INVALID_ARG;
-    }
-    if (o->solver == NN_SOLVER_LBFGS) {
-        return lbfgs_entry(s, o, nsteps, c_in, c_out, c_hist, memory, S(stream), infos, ninfos);
     }
     if (want_transient && o->precision == NN_PREC_MIXED) {
         set_error("mixed precision is available for steady systems");

@@ -1,6 +1,6 @@
 // Gradient projection + conjugate gradient (GPCG) for the box QP
 //     minimize q(x) = 1/2 x'Ax - b'x   subject to  l <= x <= h
-// (the non-negative formulation, Sec. 2.1.4, and its transient form with
+// (the non-negative formulation, Sec. 2.1.3, and its transient form with
 // c_min, c_max, Sec. 2.2.2; GPCG is the TAO method named in Sec. 3.1).
 // Algorithm after More & Toraldo (SIAM J. Optim. 1, 1991):
 //   * gradient-projection phase: steepest descent along -gP with the Cauchy
@@ -74,6 +74,8 @@ struct GpcgCtl {
     int cg_max;          // CG iterations per face
     double eta1, eta2;   // stall ratios of the GP and CG phases
     double mu;           // Armijo constant
+    int cg_variant;      // 0: textbook PCG (3 team barriers per iteration);
+                         // 1: Chronopoulos-Gear PCG (2 barriers, one fused reduction)
 };
 
 // vec counts vector streams (one read or write of an n-vector) made by the
@@ -166,6 +168,81 @@ __device__ int gpcg_solve(Team &T, const Rows &R, const Op &A, const Bounds<V> &
         if (st.gp2 <= tol2 || st.spmv >= C.max_spmv || !isfinite(st.gp2)) continue;
         // ------------------------------------------------ CG on faces
         for (;;) {
+            if (C.cg_variant == 1) {
+                // Chronopoulos-Gear form: one fused reduction per iteration
+                // (gamma = r'u and delta = w'u with u = D^-1 r, w = A_F u), the
+                // product A p carried by the recurrence q = w + beta q.
+                R.each([&](int64_t i) {
+                    V xi = v.x[i];
+                    bool fr = xi > B.l(i) && xi < B.h(i);
+                    V ri = fr ? -v.g[i] : (V)0;
+                    v.r[i] = ri;
+                    v.z[i] = v.dinv[i] * ri;
+                    v.s[i] = (V)0;
+                    v.p[i] = (V)0;
+                    v.q[i] = (V)0;
+                });
+                st.vec += 8;
+                if (!T.sync()) return ST_TIMEOUT;
+                double c3[4] = {0.0, 0.0, 0.0, 0.0};   // gamma, delta, r'r, bound crossings
+                A.apply(R, v.z, [&](int64_t i, V au) {
+                    V xi = v.x[i];
+                    V wi = (xi > B.l(i) && xi < B.h(i)) ? au : (V)0;
+                    v.w[i] = wi;
+                    V ri = v.r[i];
+                    c3[0] += (double)ri * (double)v.z[i];
+                    c3[1] += (double)wi * (double)v.z[i];
+                });
+                if (!T.reduce(c3)) return ST_TIMEOUT;
+                ++st.spmv;
+                st.vec += 3;
+                double gamma = c3[0], delta = c3[1];
+                if (!(gamma > 0.0) || !(delta > 0.0)) break;
+                double alpha = gamma / delta, beta = 0.0, maxdec = 0.0;
+                for (int k = 0; k < C.cg_max; ++k) {
+                    const V va = (V)alpha, vb = (V)beta;
+                    double c4[4] = {0.0, 0.0, 0.0, 0.0};
+                    R.each([&](int64_t i) {
+                        V pi = v.z[i] + vb * v.p[i];
+                        V qi = v.w[i] + vb * v.q[i];
+                        V si = v.s[i] + va * pi;
+                        V ri = v.r[i] - va * qi;
+                        v.p[i] = pi;
+                        v.q[i] = qi;
+                        v.s[i] = si;
+                        v.r[i] = ri;
+                        v.z[i] = v.dinv[i] * ri;
+                        V xs = v.x[i] + si;
+                        c4[3] += (xs < B.l(i) || xs > B.h(i)) ? 1.0 : 0.0;
+                    });
+                    st.vec += 13;
+                    if (!T.sync()) return ST_TIMEOUT;
+                    A.apply(R, v.z, [&](int64_t i, V au) {
+                        V xi = v.x[i];
+                        V wi = (xi > B.l(i) && xi < B.h(i)) ? au : (V)0;
+                        v.w[i] = wi;
+                        V ri = v.r[i], ui = v.z[i];
+                        c4[0] += (double)ri * (double)ui;
+                        c4[1] += (double)wi * (double)ui;
+                        c4[2] += (double)ri * (double)ri;
+                    });
+                    if (!T.reduce(c4)) return ST_TIMEOUT;
+                    ++st.spmv;
+                    ++st.cg;
+                    st.vec += 3;
+                    const double dec = 0.5 * alpha * gamma;
+                    if (dec > maxdec) maxdec = dec;
+                    const double gnew = c4[0];
+                    if (c4[3] > 0.0 || dec <= C.eta2 * maxdec || c4[2] <= ftol2 || st.spmv >= C.max_spmv ||
+                        !(gnew > 0.0))
+                        break;
+                    beta = gnew / gamma;
+                    const double den = c4[1] - beta * gnew / alpha;
+                    if (!(den > 0.0)) break;
+                    alpha = gnew / den;
+                    gamma = gnew;
+                }
+            } else {
             double a3[1] = {0.0};
             R.each([&](int64_t i) {
                 V xi = v.x[i];
@@ -224,6 +301,7 @@ __device__ int gpcg_solve(Team &T, const Rows &R, const Op &A, const Bounds<V> &
                 st.vec += 3;
                 if (!T.sync()) return ST_TIMEOUT;
             }
+            }  // CG variants
             // projected search along the CG step s
             double alpha = 1.0;
             bool accepted = false;

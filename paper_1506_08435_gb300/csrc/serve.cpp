@@ -1,0 +1,390 @@
+// Serving loop: continuous admission of steady QP requests.
+//
+// Requests are queued by nn_serve_submit (host arrays copied at once).  A
+// scheduler thread admits the oldest queued request when (a) a worker slot
+// is free, (b) its device-memory estimate fits in the HBM budget next to the
+// requests already resident, and (c) its persistent solve grid fits in the
+// SM-block budget next to the grids of the requests already running.  Each
+// worker owns a CUDA stream: it assembles the request's system, solves it in
+// one persistent launch and copies the solution back, so the device work of
+// different requests overlaps.  Because the grids of all running solves fit
+// on the device together, no solve ever waits for blocks that cannot
+// become resident.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <vector>
+#include "internal.h"
+
+namespace nnqp {
+
+nn_status assemble_impl(const nn_problem *p, const nn_assemble_opts *o, cudaStream_t st, nn_system **out);
+nn_status check_opts(const nn_solve_opts *o);
+nn_status serve_solve(nn_system *s, const nn_solve_opts *o, const double *c_in_dev, double *c_out_dev,
+                      cudaStream_t st, int grid_blocks, nn_solve_info *info);
+int solve_grid_capacity();
+
+using Clock = std::chrono::steady_clock;
+
+struct Request {
+    uint64_t id = 0;
+    nn_problem p{};
+    std::vector<double> coords, coef, fel, dval;
+    std::vector<int32_t> conn;
+    std::vector<uint8_t> dmask;
+    int64_t N = 0, E = 0;
+    size_t bytes = 0;
+    int blocks = 0;
+    Clock::time_point t_submit, t_done;
+    std::vector<double> result;
+    nn_solve_info info{};
+    nn_status status = NN_ERR_BUSY;
+    bool done = false;
+};
+
+struct Server {
+    size_t budget = 0;
+    nn_serve_opts opts{};
+    int device = 0;
+    int capacity = 0;             // co-resident blocks of the solve kernel on the device
+    std::mutex mu;
+    std::condition_variable cv_sched, cv_done;
+    std::deque<std::shared_ptr<Request>> queue;
+    std::map<uint64_t, std::shared_ptr<Request>> table;
+    std::deque<std::shared_ptr<Request>> ready;      // admitted, waiting for a worker
+    uint64_t next_id = 1;
+    size_t resident = 0, peak = 0;
+    int blocks_in_use = 0;
+    int inflight = 0;
+    int64_t inflight_peak = 0;
+    int64_t submitted = 0, completed = 0, failed = 0, rejected = 0;
+    std::vector<double> lat_ms;
+    Clock::time_point first_submit, last_done;
+    bool have_first = false;
+    bool stop = false;
+    std::thread sched;
+    std::vector<std::thread> workers;
+};
+
+namespace {
+
+// Upper estimate of the device bytes one request holds while it runs.
+size_t estimate_bytes(int dim, int64_t N, int64_t E) {
+    const double nnz = (dim == 3 ? 16.0 : 7.5) * (double)N;
+    const double b = 52.0 * nnz + 300.0 * N + (dim == 3 ? 150.0 : 110.0) * E + (4 << 20);
+    return (size_t)b;
+}
+
+void worker_loop(Server *sv) {
+    cudaSetDevice(sv->device);
+    cudaStream_t st;
+    cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    for (;;) {
+        std::shared_ptr<Request> r;
+        {
+            std::unique_lock<std::mutex> lk(sv->mu);
+            sv->cv_sched.wait(lk, [&] { return sv->stop || !sv->ready.empty(); });
+            if (sv->stop && sv->ready.empty()) break;
+            r = sv->ready.front();
+            sv->ready.pop_front();
+        }
+        nn_assemble_opts ao;
+        nn_assemble_opts_default(&ao);
+        ao.build_mixed = sv->opts.solve.precision == NN_PREC_MIXED;
+        nn_system *s = nullptr;
+        nn_status stt = assemble_impl(&r->p, &ao, st, &s);
+        double *dc = nullptr;
+        if (stt == NN_OK) {
+            if (cudaMallocAsync(&dc, sizeof(double) * r->N, st) != cudaSuccess) stt = NN_ERR_OOM;
+        }
+        if (stt == NN_OK) {
+            cudaMemsetAsync(dc, 0, sizeof(double) * r->N, st);
+            stt = serve_solve(s, &sv->opts.solve, dc, dc, st, r->blocks, &r->info);
+            if (stt == NN_OK || stt == NN_ERR_NOT_CONVERGED) {
+                r->result.resize(r->N);
+                if (cudaMemcpyAsync(r->result.data(), dc, sizeof(double) * r->N, cudaMemcpyDeviceToHost, st) !=
+                        cudaSuccess ||
+                    cudaStreamSynchronize(st) != cudaSuccess)
+                    stt = NN_ERR_CUDA;
+            }
+        }
+        if (dc) cudaFreeAsync(dc, st);
+        if (s) {
+            s->arena.release(st);
+            delete s;
+        }
+        cudaStreamSynchronize(st);
+        {
+            std::lock_guard<std::mutex> lk(sv->mu);
+            r->status = stt;
+            r->info.status = stt;
+            r->t_done = Clock::now();
+            r->done = true;
+            sv->resident -= r->bytes;
+            sv->blocks_in_use -= r->blocks;
+            --sv->inflight;
+            if (stt == NN_OK) {
+                ++sv->completed;
+                sv->lat_ms.push_back(std::chrono::duration<double, std::milli>(r->t_done - r->t_submit).count());
+                sv->last_done = r->t_done;
+            } else {
+                ++sv->failed;
+            }
+            // drop the copied input arrays now; the result stays until polled
+            r->coords.clear(); r->coef.clear(); r->fel.clear(); r->dval.clear(); r->conn.clear(); r->dmask.clear();
+        }
+        sv->cv_sched.notify_all();
+        sv->cv_done.notify_all();
+    }
+    cudaStreamDestroy(st);
+}
+
+void sched_loop(Server *sv) {
+    std::unique_lock<std::mutex> lk(sv->mu);
+    for (;;) {
+        sv->cv_sched.wait(lk, [&] {
+            if (sv->stop) return true;
+            if (sv->queue.empty()) return false;
+            const auto &r = sv->queue.front();
+            return sv->inflight < sv->opts.max_inflight && sv->resident + r->bytes <= sv->budget &&
+                   sv->blocks_in_use + r->blocks <= sv->capacity;
+        });
+        if (sv->stop) break;
+        auto r = sv->queue.front();
+        sv->queue.pop_front();
+        sv->resident += r->bytes;
+        sv->peak = std::max(sv->peak, sv->resident);
+        sv->blocks_in_use += r->blocks;
+        ++sv->inflight;
+        sv->inflight_peak = std::max<int64_t>(sv->inflight_peak, sv->inflight);
+        sv->ready.push_back(r);
+        sv->cv_sched.notify_all();
+    }
+}
+
+}  // namespace
+}  // namespace nnqp
+
+using namespace nnqp;
+
+struct nn_server {
+    Server s;
+};
+
+extern "C" {
+
+void nn_serve_opts_default(nn_serve_opts *o) {
+    if (!o) return;
+    o->max_inflight = 8;
+    o->queue_capacity = 100000;
+    o->sm_share_blocks = 0;
+    nn_solve_opts_default(&o->solve);
+}
+
+nn_status nn_serve_create(size_t hbm_budget_bytes, const nn_serve_opts *o, nn_server **out) {
+    clear_error();
+    if (!out || hbm_budget_bytes == 0) {
+        set_error("nn_serve_create: out and a nonzero budget are required");
+        return NN_ERR_INVALID_ARG;
+    }
+    nn_serve_opts d;
+    nn_serve_opts_default(&d);
+    if (!o) o = &d;
+    NN_TRY(check_opts(&o->solve));
+    if (o->max_inflight < 1 || o->max_inflight > 64 || o->queue_capacity < 1 ||
+        o->solve.solver != NN_SOLVER_GPCG || o->solve.format != NN_FMT_SELL) {
+        set_error("nn_serve_create: 1 <= max_inflight <= 64, queue_capacity >= 1, GPCG on SELL");
+        return NN_ERR_INVALID_ARG;
+    }
+    nn_server *h = new nn_server();
+    Server *sv = &h->s;
+    sv->budget = hbm_budget_bytes;
+    sv->opts = *o;
+    cudaGetDevice(&sv->device);
+    sv->capacity = solve_grid_capacity();
+    if (sv->capacity < 1) {
+        delete h;
+        set_error("nn_serve_create: cannot size the solve kernel on this device");
+        return NN_ERR_CUDA;
+    }
+    sv->sched = std::thread(sched_loop, sv);
+    for (int i = 0; i < o->max_inflight; ++i) sv->workers.emplace_back(worker_loop, sv);
+    *out = h;
+    return NN_OK;
+}
+
+nn_status nn_serve_submit(nn_server *h, const nn_problem *p, uint64_t *request_id) {
+    clear_error();
+    if (!h || !p || !request_id) {
+        set_error("nn_serve_submit: NULL argument");
+        return NN_ERR_INVALID_ARG;
+    }
+    Server *sv = &h->s;
+    if (p->memory != NN_MEM_HOST) {
+        set_error("nn_serve_submit: requests carry host arrays");
+        return NN_ERR_INVALID_ARG;
+    }
+    if ((p->dim != 2 && p->dim != 3) || !p->coef || !p->dirichlet_mask || !p->dirichlet_value) {
+        set_error("nn_serve_submit: dim 2|3, coef and Dirichlet arrays are required");
+        return NN_ERR_INVALID_ARG;
+    }
+    if (std::isnan(p->lo) || std::isnan(p->hi) || p->lo > p->hi) {
+        set_error("nn_serve_submit: bounds must satisfy lo <= hi");
+        return NN_ERR_INFEASIBLE;
+    }
+    if (p->dt != 0.0) {
+        set_error("nn_serve_submit: serving takes steady problems");
+        return NN_ERR_INVALID_ARG;
+    }
+    auto r = std::make_shared<Request>();
+    const int dim = p->dim, nv = dim + 1;
+    if (p->coords) {
+        r->N = p->n_nodes;
+        r->E = p->n_elems;
+    } else {
+        NN_TRY(nn_mesh_counts(dim, p->nx, p->ny, p->nz, &r->N, &r->E));
+    }
+    if (r->N < 1 || r->E < 1) {
+        set_error("nn_serve_submit: empty mesh");
+        return NN_ERR_INVALID_ARG;
+    }
+    r->bytes = estimate_bytes(dim, r->N, r->E);
+    if (r->bytes > sv->budget) {
+        set_error("nn_serve_submit: the request alone (%zu bytes) exceeds the budget", r->bytes);
+        return NN_ERR_INVALID_ARG;
+    }
+    // persistent grid: a fixed share, or one block per 8 slices, within the share
+    const int64_t slices = (r->N + 31) / 32;
+    const int share = sv->opts.sm_share_blocks > 0 ? sv->opts.sm_share_blocks
+                                                   : std::max(1, sv->capacity / sv->opts.max_inflight);
+    r->blocks = (int)std::max<int64_t>(1, std::min<int64_t>((slices + 7) / 8, std::min(share, sv->capacity)));
+    const int ncoef = p->coef_kind == NN_COEF_TENSOR ? (dim == 2 ? 3 : 6) : dim;
+    r->coef.assign(p->coef, p->coef + (size_t)r->E * ncoef);
+    if (p->f_elem) r->fel.assign(p->f_elem, p->f_elem + r->E);
+    r->dmask.assign(p->dirichlet_mask, p->dirichlet_mask + r->N);
+    r->dval.assign(p->dirichlet_value, p->dirichlet_value + r->N);
+    if (p->coords) {
+        r->coords.assign(p->coords, p->coords + (size_t)r->N * dim);
+        r->conn.assign(p->conn, p->conn + (size_t)r->E * nv);
+    }
+    r->p = *p;
+    r->p.coef = r->coef.data();
+    r->p.f_elem = p->f_elem ? r->fel.data() : nullptr;
+    r->p.dirichlet_mask = r->dmask.data();
+    r->p.dirichlet_value = r->dval.data();
+    r->p.coords = p->coords ? r->coords.data() : nullptr;
+    r->p.conn = p->coords ? r->conn.data() : nullptr;
+    r->t_submit = Clock::now();
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        if ((int64_t)sv->queue.size() >= sv->opts.queue_capacity) {
+            ++sv->rejected;
+            set_error("nn_serve_submit: queue full");
+            return NN_ERR_BUSY;
+        }
+        r->id = sv->next_id++;
+        sv->table[r->id] = r;
+        sv->queue.push_back(r);
+        ++sv->submitted;
+        if (!sv->have_first) {
+            sv->first_submit = r->t_submit;
+            sv->have_first = true;
+        }
+    }
+    sv->cv_sched.notify_all();
+    *request_id = r->id;
+    return NN_OK;
+}
+
+nn_status nn_serve_poll(nn_server *h, uint64_t id, double *c_out, nn_solve_info *info) {
+    clear_error();
+    if (!h) {
+        set_error("nn_serve_poll: NULL server");
+        return NN_ERR_INVALID_ARG;
+    }
+    Server *sv = &h->s;
+    std::shared_ptr<Request> r;
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        auto it = sv->table.find(id);
+        if (it == sv->table.end()) {
+            set_error("nn_serve_poll: unknown request %llu", (unsigned long long)id);
+            return NN_ERR_INVALID_ARG;
+        }
+        r = it->second;
+        if (!r->done) return NN_ERR_BUSY;
+        sv->table.erase(it);
+    }
+    if (info) *info = r->info;
+    if (r->status != NN_OK && r->status != NN_ERR_NOT_CONVERGED) {
+        set_error("request %llu failed with status %d", (unsigned long long)id, (int)r->status);
+        return r->status;
+    }
+    if (c_out) std::memcpy(c_out, r->result.data(), sizeof(double) * r->N);
+    return r->status;
+}
+
+nn_status nn_serve_drain(nn_server *h) {
+    if (!h) return NN_ERR_INVALID_ARG;
+    Server *sv = &h->s;
+    std::unique_lock<std::mutex> lk(sv->mu);
+    sv->cv_done.wait(lk, [&] { return sv->completed + sv->failed >= sv->submitted; });
+    return NN_OK;
+}
+
+nn_status nn_serve_stats(nn_server *h, nn_serve_stats_t *st) {
+    if (!h || !st) return NN_ERR_INVALID_ARG;
+    Server *sv = &h->s;
+    std::lock_guard<std::mutex> lk(sv->mu);
+    std::memset(st, 0, sizeof(*st));
+    st->submitted = sv->submitted;
+    st->completed = sv->completed;
+    st->failed = sv->failed;
+    st->rejected = sv->rejected;
+    st->bytes_resident = sv->resident;
+    st->bytes_peak = sv->peak;
+    st->budget = sv->budget;
+    st->inflight_peak = sv->inflight_peak;
+    if (!sv->lat_ms.empty()) {
+        std::vector<double> v = sv->lat_ms;
+        std::sort(v.begin(), v.end());
+        auto pct = [&](double q) {
+            const double pos = q * (v.size() - 1);
+            const size_t i = (size_t)pos;
+            const double f = pos - i;
+            return i + 1 < v.size() ? v[i] * (1 - f) + v[i + 1] * f : v[i];
+        };
+        st->p50_ms = pct(0.50);
+        st->p99_ms = pct(0.99);
+        double s = 0;
+        for (double x : v) s += x;
+        st->mean_ms = s / v.size();
+        const double span = std::chrono::duration<double>(sv->last_done - sv->first_submit).count();
+        st->solves_per_s = span > 0 ? sv->completed / span : 0.0;
+    }
+    return NN_OK;
+}
+
+void nn_serve_destroy(nn_server *h) {
+    if (!h) return;
+    Server *sv = &h->s;
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        sv->stop = true;
+    }
+    sv->cv_sched.notify_all();
+    if (sv->sched.joinable()) sv->sched.join();
+    for (auto &t : sv->workers)
+        if (t.joinable()) t.join();
+    delete h;
+}
+
+}  // extern "C"

@@ -9,6 +9,7 @@
 #include "internal.h"
 #include "gpcg.cuh"
 #include "refine.cuh"
+#include "lbfgs.cuh"
 
 namespace nnqp {
 
@@ -45,7 +46,54 @@ struct GridArgs {
     int bar_extra;          // arrivals the barrier waits for beyond the grid (0; 1 only in the stall test)
     int64_t *counters;      // [nsteps][kCounters]
     double *scalars;        // [nsteps][kScalars]
+    // projected L-BFGS
+    double *S, *Y;          // (m+1) slots of n doubles each
+    int m;
+    double h0;
 };
+
+// b of one backward-Euler step: b0 + M x / dt (Sec. 2.2.2, with c^(n));
+// returns ||b||_2 through den.
+template <class Team>
+__device__ bool transient_rhs(Team &T, const Rows &R, const GridArgs &a, const double *x, double *&b, double &den) {
+    double *bt = a.v64[9];
+    double acc[1] = {0.0};
+    a.M.apply(R, x, [&](int64_t i, double mx) {
+        const double bi = a.b0[i] + mx * a.inv_dt;
+        bt[i] = bi;
+        acc[0] += bi * bi;
+    });
+    if (!T.reduce(acc)) return false;
+    den = sqrt(acc[0]);
+    b = bt;
+    return true;
+}
+
+// Scatter of the step result to the full-node outputs and the per-step record.
+template <class Team>
+__device__ bool step_outputs(Team &T, const Rows &R, const GridArgs &a, const double *x, int step, int nsteps,
+                             int status, int64_t (&cnt)[kCounters], double gp2, double den) {
+    double acc[2] = {0.0, 0.0};
+    double *hist = a.c_hist ? a.c_hist + (int64_t)step * a.N : nullptr;
+    R.each([&](int64_t i) {
+        const double xi = x[i];
+        const int32_t v = a.free_node[i];
+        if (hist) hist[v] = xi;
+        if (step == nsteps - 1) a.c_out[v] = xi;
+        acc[0] += xi <= a.lo ? 1.0 : 0.0;
+        acc[1] += xi >= a.hi ? 1.0 : 0.0;
+    });
+    if (!T.reduce(acc)) return false;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        cnt[0] = status;
+        cnt[8] = (int64_t)acc[0];
+        cnt[9] = (int64_t)acc[1];
+        for (int k = 0; k < kCounters; ++k) a.counters[(int64_t)step * kCounters + k] = cnt[k];
+        a.scalars[step * kScalars + 0] = gp2;
+        a.scalars[step * kScalars + 1] = den;
+    }
+    return true;
+}
 
 template <int FMT>
 __global__ void __launch_bounds__(kSolveThreads) k_solve_grid(GridArgs a) {
@@ -60,18 +108,9 @@ __global__ void __launch_bounds__(kSolveThreads) k_solve_grid(GridArgs a) {
         int status = ST_OK;
         int64_t cnt[kCounters] = {0};
         double den = a.b0norm, gp2 = 0.0;
-        const double *b = a.b0;
+        double *b = const_cast<double *>(a.b0);
         if (a.mode == MODE_TRANSIENT) {
-            double *bt = a.v64[9];
-            double acc[1] = {0.0};
-            a.M.apply(R, x, [&](int64_t i, double mx) {
-                const double bi = a.b0[i] + mx * a.inv_dt;
-                bt[i] = bi;
-                acc[0] += bi * bi;
-            });
-            if (!T.reduce(acc)) return;
-            den = sqrt(acc[0]);
-            b = bt;
+            if (!transient_rhs(T, R, a, x, b, den)) return;
             cnt[1] += 1;   // products with M (FP64)
         }
         if (!(den > 0.0)) den = a.den_fallback;
@@ -113,26 +152,43 @@ __global__ void __launch_bounds__(kSolveThreads) k_solve_grid(GridArgs a) {
             cnt[6] = gs.vec;
             gp2 = gs.gp2;
         }
-        // outputs: scatter to the full vectors, count active entries
-        double acc[2] = {0.0, 0.0};
-        double *hist = a.c_hist ? a.c_hist + (int64_t)step * a.N : nullptr;
-        R.each([&](int64_t i) {
-            const double xi = x[i];
-            const int32_t v = a.free_node[i];
-            if (hist) hist[v] = xi;
-            if (step == nsteps - 1) a.c_out[v] = xi;
-            acc[0] += xi <= a.lo ? 1.0 : 0.0;
-            acc[1] += xi >= a.hi ? 1.0 : 0.0;
-        });
-        if (!T.reduce(acc)) return;
-        if (blockIdx.x == 0 && threadIdx.x == 0) {
-            cnt[0] = status;
-            cnt[8] = (int64_t)acc[0];
-            cnt[9] = (int64_t)acc[1];
-            for (int k = 0; k < kCounters; ++k) a.counters[(int64_t)step * kCounters + k] = cnt[k];
-            a.scalars[step * kScalars + 0] = gp2;
-            a.scalars[step * kScalars + 1] = den;
+        if (!step_outputs(T, R, a, x, step, nsteps, status, cnt, gp2, den)) return;
+    }
+}
+
+// The same driver with the projected L-BFGS solver (FP64, SELL).
+__global__ void __launch_bounds__(kSolveThreads) k_lbfgs_grid(GridArgs a) {
+    __shared__ RedSmem sm;
+    __shared__ LbSmem lsm;
+    GridTeam T{a.bar, a.partials, (int)gridDim.x + a.bar_extra, a.timeout_ns, 0, 0, &sm};
+    const Rows R = rows_of_block(a.n, a.nslices, blockIdx.x, gridDim.x);
+    double *x0 = a.v64[0];
+    R.each([&](int64_t i) { x0[i] = a.c_in[a.free_node[i]]; });
+    if (!T.sync()) return;
+    const int nsteps = a.mode == MODE_TRANSIENT ? a.nsteps : 1;
+    for (int step = 0; step < nsteps; ++step) {
+        int64_t cnt[kCounters] = {0};
+        double den = a.b0norm;
+        double *b = const_cast<double *>(a.b0);
+        if (a.mode == MODE_TRANSIENT) {
+            if (!transient_rhs(T, R, a, x0, b, den)) return;
+            cnt[1] += 1;
         }
+        if (!(den > 0.0)) den = a.den_fallback;
+        double *x = x0, *g = a.v64[1], *w = a.v64[7], *gw = a.v64[8];
+        LbCtl c{a.rtol * den, a.ctl.max_spmv, a.m, a.ctl.mu, a.h0};
+        LbStats ls;
+        const int status = lbfgs_solve(T, R, a.A, a.lo, a.hi, b, x, g, a.v64[2], w, gw, a.S, a.Y, a.n, c, ls, lsm);
+        if (status == ST_TIMEOUT) return;
+        if (x != x0) {
+            R.each([&](int64_t i) { x0[i] = x[i]; });
+            if (!T.sync()) return;
+        }
+        cnt[1] += ls.spmv;
+        cnt[4] = ls.iters;
+        cnt[6] = ls.vec;
+        cnt[10] = ls.resets;
+        if (!step_outputs(T, R, a, x0, step, nsteps, status, cnt, ls.gp2, den)) return;
     }
 }
 
@@ -351,6 +407,11 @@ nn_status run_grid(nn_system *s, const nn_solve_opts *o, int mode, int nsteps, c
     a.ctl.eta1 = 0.1;
     a.ctl.eta2 = 1e-3;
     a.ctl.mu = 1e-4;
+    a.ctl.cg_variant = n < (1 << 20) ? 1 : 0;
+    if (const char *e = getenv("NNQP_CG_VARIANT")) a.ctl.cg_variant = atoi(e);
+    if (const char *e = getenv("NNQP_GP_MAX")) a.ctl.gp_max = atoi(e);
+    if (const char *e = getenv("NNQP_ETA1")) a.ctl.eta1 = atof(e);
+    if (const char *e = getenv("NNQP_ETA2")) a.ctl.eta2 = atof(e);
     a.rtol = o->rtol;
     a.den_fallback = den_fallback(s);
     a.b0norm = s->b0norm;
@@ -358,7 +419,18 @@ nn_status run_grid(nn_system *s, const nn_solve_opts *o, int mode, int nsteps, c
     a.max_ref = 200;
     a.timeout_ns = (unsigned long long)(o->wait_timeout_s * 1e9);
     // grid
-    void (*kern)(GridArgs) = fmt == NN_FMT_CSR ? k_solve_grid<1> : k_solve_grid<0>;
+    const bool lbfgs = o->solver == NN_SOLVER_LBFGS;
+    if (lbfgs && (mixed || fmt == NN_FMT_CSR)) {
+        set_error("the projected L-BFGS solver runs in FP64 on the SELL format");
+        return NN_ERR_INVALID_ARG;
+    }
+    if (lbfgs) {
+        a.m = std::min(o->lbfgs_m, kLbMaxM);
+        a.h0 = 1.0 / s->anorm_inf;
+        NN_TRY(S.a.alloc(&a.S, (size_t)(a.m + 1) * n, st));
+        NN_TRY(S.a.alloc(&a.Y, (size_t)(a.m + 1) * n, st));
+    }
+    void (*kern)(GridArgs) = lbfgs ? k_lbfgs_grid : (fmt == NN_FMT_CSR ? k_solve_grid<1> : k_solve_grid<0>);
     const int maxg = max_coresident(kern);
     int warps = kSolveThreads / 32;
     int want = (int)std::min<int64_t>((s->A64.nslices + warps - 1) / warps, (int64_t)maxg);
@@ -514,6 +586,17 @@ nn_status solve_entry(nn_system *s, const nn_solve_opts *o, int mode, int nsteps
 int mode_for(const nn_system *s, const nn_solve_opts *o) {
     if (s->dt > 0.0) return MODE_TRANSIENT;
     return o->precision == NN_PREC_MIXED ? MODE_MIXED : MODE_STEADY;
+}
+
+// Co-resident blocks of the steady/mixed solve kernel on the current device.
+int solve_grid_capacity() { return max_coresident(k_solve_grid<0>); }
+
+// One steady solve with a fixed persistent grid (serving).
+nn_status serve_solve(nn_system *s, const nn_solve_opts *o, const double *c_in_dev, double *c_out_dev,
+                      cudaStream_t st, int grid_blocks, nn_solve_info *info) {
+    nn_solve_opts q = *o;
+    q.grid_blocks = grid_blocks;
+    return run_grid(s, &q, mode_for(s, &q), 1, c_in_dev, c_out_dev, nullptr, st, info, info ? 1 : 0);
 }
 
 }  // namespace nnqp

@@ -15,7 +15,7 @@
 
 namespace nnqp {
 
-constexpr int kMaxRed = 8;        // doubles per reduction call
+constexpr int kMaxRed = 24;       // doubles per reduction call (at most)
 constexpr int kMaxWarps = 32;
 
 struct GridBarrier {

@@ -4,7 +4,7 @@ Bit-exact: mesh coordinates/connectivity, CSR patterns, free numbering,
 active sets on nondegenerate entries.  Floating point: assembled values to
 1e-13 relative to the row's absolute sum; QP solutions to 1e-6 relative in
 the max norm with the oracle's KKT residual of the GPU vector <= 1e-8 and
-bounds exact (the acceptance of the method's QP, Sec. 2.1.4).
+bounds exact (the acceptance of the method's QP, Sec. 2.1.3).
 """
 import math
 import os
@@ -101,7 +101,9 @@ def test_assembly_pattern_bit_exact_values_close(name):
     arabs = np.repeat(np.add.reduceat(np.abs(A.data), A.indptr[:-1]), np.diff(A.indptr))
     assert np.all(np.abs(Av - A.data) <= 1e-13 * arabs)
     b0 = copy(s, "b0", NF, np.float64)
-    b_ref = red.rhs(np.zeros(N)) if spec.dt > 0 else red.rhs()
+    # transient: b0 = F_F - K_FD c_D is the step right-hand side for a state that
+    # is 0 at the free nodes (the M_FD c_D / dt terms cancel), i.e. red.rhs(c_D)
+    b_ref = red.rhs(red.full(np.zeros(NF))) if spec.dt > 0 else red.rhs()
     assert np.abs(b0 - b_ref).max() <= 1e-13 * max(np.abs(b_ref).max(), 1e-300) + 1e-300
 
 

@@ -1,0 +1,196 @@
+"""Parity of the projected L-BFGS solver, the batched persistent solve and
+the serving loop with the FP64 oracle; alone-vs-in-the-mix equality."""
+import math
+import time
+
+import numpy as np
+import pytest
+
+import nn_inputs as I
+from oracle import oracle as O
+from tests.gpu_common import compare_solution, oracle_reduced, oracle_solution
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+import paper_1506_08435_gb300 as P  # noqa: E402
+
+DEV = torch.device("cuda:0")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    P.lib()
+
+
+def gpu_system(spec, **kw):
+    return P.nn_assemble(P.Problem(spec, device=DEV), P.assemble_opts(**kw))
+
+
+# ------------------------------------------------------------------ projected L-BFGS
+
+@pytest.mark.parametrize("m", [1, 3, 5])
+def test_lbfgs_steady_matches_oracle(m):
+    spec = I.config1_steady_2d(n=30)
+    s = gpu_system(spec)
+    c = torch.zeros(spec.n_nodes, dtype=torch.float64, device=DEV)
+    info = P.nn_qp_solve(s, c, P.solve_opts(solver=P.NN_SOLVER_LBFGS, lbfgs_m=m, rtol=1e-11))
+    assert info["status"] == 0, info
+    red, b, x_ref, _ = oracle_solution(spec)
+    compare_solution(c.cpu().numpy()[red.free], x_ref, red.A, b, spec.lo, spec.hi)
+
+
+@pytest.mark.parametrize("case", ["2d_n4_box", "3d_n3_lower"])
+def test_lbfgs_matches_bruteforce(case):
+    if case == "2d_n4_box":
+        spec = I.tiny_2d(4, 4, hi=1.5e-5)
+    else:
+        Q = I.quaternion_rotation(I.SplitMix64(2, 0))
+        Dm = Q @ np.diag([1000.0, 1.0, 1.0]) @ Q.T
+        spec = I.tiny_3d(3, [Dm[0, 0], Dm[0, 1], Dm[0, 2], Dm[1, 1], Dm[1, 2], Dm[2, 2]])
+    asm, red = oracle_reduced(spec)
+    b = red.rhs()
+    (xb, assign), = O.brute_force(red.A, b, spec.lo, spec.hi)
+    s = gpu_system(spec)
+    c = torch.zeros(spec.n_nodes, dtype=torch.float64, device=DEV)
+    info = P.nn_qp_solve(s, c, P.solve_opts(solver=P.NN_SOLVER_LBFGS, rtol=1e-12))
+    x = c.cpu().numpy()[red.free]
+    assert info["status"] == 0
+    active = np.where(x == spec.lo, 1, np.where(x == spec.hi, 2, 0))
+    assert np.array_equal(active, assign)
+    assert np.abs(x - xb).max() <= 1e-9 * np.abs(xb).max()
+
+
+def test_lbfgs_transient_matches_gpcg():
+    spec = I.config2_transient_3d(n=10, nsteps=4)
+    s = gpu_system(spec)
+    outs = {}
+    for solver in (P.NN_SOLVER_GPCG, P.NN_SOLVER_LBFGS):
+        c0 = torch.tensor(spec.c0, device=DEV)
+        cf = torch.zeros_like(c0)
+        hist = torch.zeros(spec.nsteps * spec.n_nodes, dtype=torch.float64, device=DEV)
+        infos = P.nn_transient(s, c0, spec.nsteps, cf, hist, P.solve_opts(solver=solver, rtol=1e-11))
+        assert all(i["status"] == 0 for i in infos)
+        outs[solver] = hist.cpu().numpy().reshape(spec.nsteps, -1)
+    asm, red = oracle_reduced(spec)
+    ref = O.transient(red, spec.c0, spec.lo, spec.hi, spec.nsteps)
+    for n in range(spec.nsteps):
+        b = red.rhs(ref[n - 1] if n else spec.c0)
+        for solver in outs:
+            compare_solution(outs[solver][n][red.free], ref[n][red.free], red.A, b, spec.lo, spec.hi)
+
+
+# ------------------------------------------------------------------ batched persistent solve
+
+def _batch(count=24, nmin=12, nmax=40):
+    insts = [I.config4_instance(i, nmin=nmin, nmax=nmax) for i in range(count)]
+    systems = [gpu_system(sp) for sp in insts]
+    return insts, systems
+
+
+@pytest.mark.parametrize("prec", [P.NN_PREC_FP64, P.NN_PREC_MIXED])
+def test_batch_matches_oracle_per_instance(prec):
+    insts, systems = _batch()
+    cs = [torch.zeros(sp.n_nodes, dtype=torch.float64, device=DEV) for sp in insts]
+    infos = P.nn_batch_solve(systems, cs, P.solve_opts(precision=prec, rtol=1e-10))
+    assert all(i["status"] == 0 for i in infos), [i["status"] for i in infos]
+    for sp, c, inf in zip(insts, cs, infos):
+        red, b, x_ref, _ = oracle_solution(sp)
+        x = c.cpu().numpy()
+        compare_solution(x[red.free], x_ref, red.A, b, sp.lo, sp.hi)
+        assert np.array_equal(x[sp.dmask == 1], sp.dval[sp.dmask == 1])
+        assert inf["kkt_rel"] <= 1e-10
+
+
+def test_batch_equals_single_block_solve_alone():
+    """An instance gives the same result inside the batch as in a batch of
+    one (the same one-block solver, deterministic reductions)."""
+    insts, systems = _batch(count=16)
+    cs = [torch.zeros(sp.n_nodes, dtype=torch.float64, device=DEV) for sp in insts]
+    P.nn_batch_solve(systems, cs)
+    for k in (0, 5, 11):
+        alone = torch.zeros_like(cs[k])
+        P.nn_batch_solve([systems[k]], [alone])
+        assert torch.equal(alone, cs[k])
+
+
+def test_batch_autotune_picks_a_shape_and_results_hold():
+    insts, systems = _batch(count=20)
+    best = P.nn_batch_autotune(systems)
+    assert best in (128, 256, 512)
+    cs = [torch.zeros(sp.n_nodes, dtype=torch.float64, device=DEV) for sp in insts]
+    infos = P.nn_batch_solve(systems, cs, P.solve_opts(precision=P.NN_PREC_MIXED))
+    assert all(i["status"] == 0 for i in infos)
+    sp, c = insts[3], cs[3]
+    red, b, x_ref, _ = oracle_solution(sp)
+    compare_solution(c.cpu().numpy()[red.free], x_ref, red.A, b, sp.lo, sp.hi)
+
+
+# ------------------------------------------------------------------ serving
+
+def _serve_specs(count=10):
+    out = []
+    r = 0
+    while len(out) < count:
+        sp = I.serve_request(r)
+        r += 1
+        if sp.n_nodes <= 30000:
+            out.append(sp)
+    return out
+
+
+def _serve(specs, max_inflight, share=16, budget=8 << 30):
+    sv = P.nn_serve_create(budget, P.serve_opts(max_inflight=max_inflight, sm_share_blocks=share))
+    ids = [P.nn_serve_submit(sv, P.Problem(sp)) for sp in specs]
+    P.nn_serve_drain(sv)
+    res = []
+    for rid, sp in zip(ids, specs):
+        c = np.zeros(sp.n_nodes)
+        info = P.nn_serve_poll(sv, rid, c)
+        res.append((c, info))
+    st = P.nn_serve_stats(sv)
+    P.nn_serve_destroy(sv)
+    return res, st
+
+
+def test_serving_results_alone_and_in_the_mix_are_identical_and_correct():
+    specs = _serve_specs(10)
+    alone, st1 = _serve(specs, max_inflight=1)
+    mixed, st8 = _serve(specs, max_inflight=8)
+    assert st1["completed"] == st8["completed"] == len(specs)
+    assert st8["inflight_peak"] > 1, "requests must overlap on the device"
+    assert st1["inflight_peak"] == 1
+    for (c1, i1), (c2, i2), sp in zip(alone, mixed, specs):
+        assert i1["status"] == 0 and i2["status"] == 0
+        assert np.array_equal(c1, c2)          # same grid share, deterministic reductions
+    for (c, _), sp in list(zip(mixed, specs))[:4]:
+        red, b, x_ref, _ = oracle_solution(sp)
+        compare_solution(c[red.free], x_ref, red.A, b, sp.lo, sp.hi)
+    assert st8["p50_ms"] > 0 and st8["p99_ms"] >= st8["p50_ms"]
+
+
+def test_serving_budget_admission_and_rejection():
+    specs = _serve_specs(6)
+    sizes = sorted(sp.n_nodes for sp in specs)
+    # a budget that fits one request at a time: admission must serialise them
+    sv = P.nn_serve_create(400 << 20, P.serve_opts(max_inflight=8, sm_share_blocks=8))
+    ids = [P.nn_serve_submit(sv, P.Problem(sp)) for sp in specs]
+    P.nn_serve_drain(sv)
+    st = P.nn_serve_stats(sv)
+    assert st["completed"] == len(specs)
+    assert st["bytes_peak"] <= st["budget"]
+    for rid, sp in zip(ids, specs):
+        assert P.nn_serve_poll(sv, rid, np.zeros(sp.n_nodes))["status"] == 0
+    # a request larger than the whole budget is refused at submit
+    big = I.config3_steady_3d(n=60, seed=1)
+    with pytest.raises(P.NnError) as e:
+        P.nn_serve_submit(sv, P.Problem(big))
+    assert e.value.status == P.NN_ERR_INVALID_ARG
+    # invalid problems are refused at submit
+    bad = I.serve_request(0)
+    bad.lo, bad.hi = 1.0, 0.0
+    with pytest.raises(P.NnError):
+        P.nn_serve_submit(sv, P.Problem(bad))
+    P.nn_serve_destroy(sv)

@@ -267,7 +267,7 @@ def test_patch_test_linear_solution_is_exact(dim):
 
 def test_qp_equals_galerkin_when_dmp_holds():
     """D = I on the '/' grid gives an M-matrix; with f >= 0 and c^p >= 0 the
-    Galerkin solution is already non-negative (Sec. 2.1.2 maximum principle),
+    Galerkin solution is already non-negative (Sec. 2.1.1 maximum principle),
     so the QP minimiser must coincide with it."""
     n = 24
     E = 2 * n * n

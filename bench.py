@@ -1,28 +1,33 @@
 """Benchmark of the non-negative diffusion QP path on GB300.
 
-Default workload (N = 1): the 3D transient problem -- unit cube, 40^3
-hexahedra x 6 tetrahedra (68,921 nodes), dispersion tensor from the vortex
-velocity field (alpha_L = 1, alpha_T = 1e-3, D_M = 1e-9), c = 1 on the
-x = 0 patch and c = 0 on x = 1, 0 <= c <= 1, backward Euler dt = 0.01 over
-50 steps, one warm-started QP per step, FP64.  One benchmark step is the
-whole path on one synthetic input: device assembly (pattern, element
+Default workload (no flags, N = 1): the 3D transient problem -- unit cube,
+40^3 hexahedra x 6 tetrahedra (68,921 nodes), dispersion tensor from the
+vortex velocity field (alpha_L = 1, alpha_T = 1e-3, D_M = 1e-9), c = 1 on
+the x = 0 patch and c = 0 on x = 1, 0 <= c <= 1, backward Euler dt = 0.01
+over 50 steps, one warm-started QP per step, FP64.  One benchmark step is
+the whole path on one synthetic input: device assembly (pattern, element
 matrices, elimination, SELL build) + the 50-step transient run in one
-persistent launch (every QP to KKT <= 1e-10 relative, which is tighter than
-the 1e-8 acceptance).
+persistent launch (every QP to KKT <= 1e-10 relative, tighter than the
+1e-8 acceptance).  metric: QP solves per second (50 per step).  The inputs
+(about 12 MB) fit in L2, so L2 is flushed between timed steps (256 MB write).
 
-metric: QP solves per second (50 per step).  The inputs (about 12 MB) fit
-in L2, so L2 is flushed between timed steps by writing a 256 MB buffer.
-
-Other workloads (--workload): steady3d (150^3 x 6 tets, FP64 or mixed),
-steady2d (the 2D 50 x 50 problem), batch (512 2D instances), serve.
+Other workloads (--workload), each printing its own line:
+  steady3d  config 3 (150^3 x 6 tets; --n to shrink), --precision fp64|mixed,
+            --solver gpcg|lbfgs; a step = assembly + one solve
+  steady2d  config 1 (50 x 50, 2D); a step = assembly + one solve
+  batch     config 4 (512 2D instances, one persistent launch); a step =
+            one batched solve of all instances, --precision fp64|mixed
+  serve     config 5 (Poisson arrivals); reports p50/p99 latency
 """
 from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import subprocess
 import sys
+import threading
 import time
 
 import numpy as np
@@ -34,6 +39,7 @@ import nn_inputs as I  # noqa: E402
 
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM = 6800.0
+FP64_FMA_PEAK_TFLOPS = 1.21   # measured register-only FMA chains on this machine's GB300
 
 
 def peaks():
@@ -121,9 +127,9 @@ class ClockSampler:
 
 # ---------------------------------------------------------------- the oracle baseline (CPU)
 
-def oracle_sample(workload, budget_s=20.0):
+def oracle_sample(workload, budget_s=20.0, n=None):
     """The FP64 oracle as it stands, on a bounded sample of the workload;
-    returns (QP solves per second, cores, description)."""
+    returns (units per second, cores used, description)."""
     from oracle import oracle as O
     threads = os.cpu_count() or 1
     if workload == "transient3d":
@@ -132,27 +138,76 @@ def oracle_sample(workload, budget_s=20.0):
         asm = O.assemble(coords, conn, spec.coef_kind, spec.coef, spec.aL, spec.aT, spec.DM, with_mass=True)
         red = O.Reduced(asm, spec.dmask, spec.dval, dt=spec.dt)
         c = spec.c0.copy()
-        t0, n = time.perf_counter(), 0
-        while n < 1 or (time.perf_counter() - t0 < budget_s and n < spec.nsteps):
+        t0, k = time.perf_counter(), 0
+        while k < 1 or (time.perf_counter() - t0 < budget_s and k < spec.nsteps):
             b = red.rhs(c)
             x, _ = O.solve_qp(red.A, b, spec.lo, spec.hi, x0=c[red.free], threads=threads)
             c = red.full(x)
-            n += 1
+            k += 1
         dt = time.perf_counter() - t0
-        return n / dt, threads, "first %d backward-Euler QP steps of the 40^3 transient problem (MPRGP + " \
-                                "polish to 1e-12, OpenMP products), assembly excluded" % n
+        return k / dt, threads, ("first %d backward-Euler QP steps of the 40^3 transient problem (MPRGP + "
+                                 "active-set polish to 1e-12, OpenMP products), assembly excluded" % k)
     if workload == "steady2d":
         spec = I.config1_steady_2d()
         coords, conn = O.mesh_structured(2, spec.nx)
         asm = O.assemble(coords, conn, spec.coef_kind, spec.coef, f_elem=spec.f_elem)
         red = O.Reduced(asm, spec.dmask, spec.dval)
         b = red.rhs()
-        t0, n = time.perf_counter(), 0
-        while n < 1 or time.perf_counter() - t0 < min(budget_s, 5.0):
+        t0, k = time.perf_counter(), 0
+        while k < 1 or time.perf_counter() - t0 < min(budget_s, 5.0):
             O.solve_qp(red.A, b, spec.lo, spec.hi, threads=1)
-            n += 1
-        return n / (time.perf_counter() - t0), 1, "%d full solves of the 2D 50x50 problem" % n
+            k += 1
+        return k / (time.perf_counter() - t0), 1, "%d full solves of the 2D 50x50 problem (1 thread)" % k
+    if workload == "batch":
+        t0, k = time.perf_counter(), 0
+        while k < 1 or time.perf_counter() - t0 < budget_s:
+            spec = I.config4_instance(k)
+            coords, conn = O.mesh_structured(2, spec.nx)
+            asm = O.assemble(coords, conn, spec.coef_kind, spec.coef, f_elem=spec.f_elem)
+            red = O.Reduced(asm, spec.dmask, spec.dval)
+            O.solve_qp(red.A, red.rhs(), spec.lo, spec.hi, threads=threads)
+            k += 1
+        return k / (time.perf_counter() - t0), threads, "first %d instances of the 512-instance batch" % k
     return None, threads, "no oracle sample for this workload"
+
+
+# ---------------------------------------------------------------- helpers
+
+def pinned_problem(P, torch, spec):
+    """A Problem whose arrays are in pinned host memory (for the e2e leg)."""
+    hp = P.Problem(spec)
+    keep = {}
+    for name in ("coef", "dmask", "dval", "f_elem"):
+        a = getattr(hp, name)
+        if a is None:
+            continue
+        t = torch.from_numpy(a).pin_memory()
+        keep[name] = t
+        setattr(hp, name, t)
+    hp.c.coef = keep["coef"].data_ptr()
+    hp.c.dirichlet_mask = keep["dmask"].data_ptr()
+    hp.c.dirichlet_value = keep["dval"].data_ptr()
+    if "f_elem" in keep:
+        hp.c.f_elem = keep["f_elem"].data_ptr()
+    hp.c.memory = P.NN_MEM_HOST
+    nbytes = sum(t.numel() * t.element_size() for t in keep.values())
+    return hp, nbytes
+
+
+def timed_steps(torch, step, steps, flush, clk):
+    stream = torch.cuda.current_stream()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    outs = []
+    clk.start()
+    time.sleep(0.3)
+    for k in range(steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        outs.append(step())
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    clocks = clk.stop(torch.cuda.current_device())
+    return [a.elapsed_time(b) for a, b in ev], outs, clocks
 
 
 # ---------------------------------------------------------------- workloads
@@ -160,11 +215,10 @@ def oracle_sample(workload, budget_s=20.0):
 def run_transient(P, torch, args, rank):
     spec = I.config2_transient_3d()
     dev = torch.device("cuda")
-    stream = torch.cuda.current_stream()
     nsteps = spec.nsteps
     prob = P.Problem(spec, device=dev)
-    opts = P.solve_opts(rtol=args.rtol)
-    aopts = P.assemble_opts(build_mixed=0, keep_full=1)
+    opts = P.solve_opts(rtol=args.rtol, solver=P.NN_SOLVER_LBFGS if args.solver == "lbfgs" else P.NN_SOLVER_GPCG)
+    aopts = P.assemble_opts(build_mixed=0)
     c0 = torch.tensor(spec.c0, device=dev)
     cf = torch.zeros_like(c0)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
@@ -172,66 +226,170 @@ def run_transient(P, torch, args, rank):
     def step():
         s = P.nn_assemble(prob, aopts)
         infos = P.nn_transient(s, c0, nsteps, cf, None, opts)
-        return s, infos
+        del s
+        return infos
 
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
-    launches0 = P.kernel_launches()
-    times, kern_ms, kern_bytes, statuses, spmv, kkt = [], [], [], [], 0, []
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    clk = ClockSampler(os.path.join(args.out_dir, "clocks_rank%d.csv" % rank))
-    clk.start()
-    time.sleep(0.3)
-    for k in range(args.steps):
-        flush.zero_()
-        ev[k][0].record(stream)
-        s, infos = step()
-        ev[k][1].record(stream)
-        kern_ms.append(infos[0]["time_ms"])
-        kern_bytes.append(sum(i["bytes_algo"] for i in infos))
-        statuses += [i["status"] for i in infos]
-        spmv += sum(i["spmv"] for i in infos)
-        kkt.append(max(i["kkt_rel"] for i in infos))
-        del s
-    torch.cuda.synchronize()
-    clocks = clk.stop(torch.cuda.current_device())
-    launches = P.kernel_launches() - launches0
-    times = [a.elapsed_time(b) for a, b in ev]
-    # end to end through the C ABI with host buffers (pinned), copies inside the timed region
-    hp = P.Problem(spec)
-    pinned = {}
-    for name in ("coef", "dmask", "dval"):
-        a = getattr(hp, name)
-        t = torch.from_numpy(a).pin_memory()
-        pinned[name] = t
-    hp2 = P.Problem(spec)
-    hp2.coef, hp2.dmask, hp2.dval = pinned["coef"], pinned["dmask"], pinned["dval"]
-    hp2.c.coef, hp2.c.dirichlet_mask, hp2.c.dirichlet_value = (pinned["coef"].data_ptr(), pinned["dmask"].data_ptr(),
-                                                               pinned["dval"].data_ptr())
-    hp2.c.memory = P.NN_MEM_HOST
+    l0 = P.kernel_launches()
+    times, outs, clocks = timed_steps(torch, step, args.steps, flush,
+                                      ClockSampler(os.path.join(args.out_dir, "clocks_rank%d.csv" % rank)))
+    launches = P.kernel_launches() - l0
+    infos = [i for o in outs for i in o]
+    # end to end through the C ABI with pinned host buffers, copies inside the timed region
+    hp, hbytes = pinned_problem(P, torch, spec)
     c0h = torch.from_numpy(spec.c0.copy()).pin_memory()
     cfh = torch.zeros_like(c0h).pin_memory()
+    stream = torch.cuda.current_stream()
     e2e = []
-    for k in range(max(args.steps, 1)):
+    for _ in range(args.steps):
         flush.zero_()
         torch.cuda.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        s = P.nn_assemble(hp2, aopts)
+        s = P.nn_assemble(hp, aopts)
         P.nn_transient(s, c0h, nsteps, cfh, None, opts)
         b.record(stream)
         torch.cuda.synchronize()
         e2e.append(a.elapsed_time(b))
         del s
-    h2d = sum(pinned[n].numel() * pinned[n].element_size() for n in pinned) + c0h.numel() * 8
-    d2h = cfh.numel() * 8
-    return dict(times=times, kern_ms=kern_ms, kern_bytes=kern_bytes, statuses=statuses, spmv=spmv, kkt=kkt,
-                units_per_step=nsteps, e2e=e2e, h2d=h2d, d2h=d2h, clocks=clocks, launches=launches,
+    return dict(times=times, infos=infos, kern_ms=[o[0]["time_ms"] for o in outs],
+                kern_bytes=[sum(i["bytes_algo"] for i in o) for o in outs], units_per_step=nsteps, e2e=e2e,
+                h2d=hbytes + c0h.numel() * 8, d2h=cfh.numel() * 8, clocks=clocks, launches=launches,
+                nnz_free=None,
                 config={"workload": "transient3d_n40_dt0.01_50steps", "nodes": spec.n_nodes,
                         "tets": spec.n_elems, "qp_per_step": nsteps, "rtol": args.rtol,
-                        "l2": "flushed between steps (256 MB write)", "solver": "gpcg", "precision": "fp64"},
-                dtype="f64", n=int(68921 - 0), nnz=None)
+                        "l2": "flushed between steps (256 MB write)", "solver": args.solver, "precision": "fp64"},
+                dtype="f64", unit="QP solves/s", metric="QP solves/s")
+
+
+def run_steady(P, torch, args, rank, dim):
+    if dim == 3:
+        spec = I.config3_steady_3d(n=args.n or 150)
+    else:
+        spec = I.config1_steady_2d(n=args.n or 50)
+    dev = torch.device("cuda")
+    prec = P.NN_PREC_MIXED if args.precision == "mixed" else P.NN_PREC_FP64
+    opts = P.solve_opts(rtol=args.rtol, precision=prec, max_iter=args.max_iter,
+                        solver=P.NN_SOLVER_LBFGS if args.solver == "lbfgs" else P.NN_SOLVER_GPCG)
+    aopts = P.assemble_opts(build_mixed=1 if prec == P.NN_PREC_MIXED else 0)
+    prob = P.Problem(spec, device=dev)
+    c = torch.zeros(spec.n_nodes, dtype=torch.float64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    desc = {}
+
+    def step():
+        s = P.nn_assemble(prob, aopts)
+        c.zero_()
+        info = P.nn_qp_solve(s, c, opts)
+        desc.update(s.describe())
+        del s
+        return [info]
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    l0 = P.kernel_launches()
+    times, outs, clocks = timed_steps(torch, step, args.steps, flush,
+                                      ClockSampler(os.path.join(args.out_dir, "clocks_rank%d.csv" % rank)))
+    launches = P.kernel_launches() - l0
+    infos = [i for o in outs for i in o]
+    hp, hbytes = pinned_problem(P, torch, spec)
+    ch = torch.zeros(spec.n_nodes, dtype=torch.float64).pin_memory()
+    stream = torch.cuda.current_stream()
+    e2e = []
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        s = P.nn_assemble(hp, aopts)
+        ch.zero_()
+        P.nn_qp_solve(s, ch, opts)
+        b.record(stream)
+        torch.cuda.synchronize()
+        e2e.append(a.elapsed_time(b))
+        del s
+    name = ("steady3d_n%d" % (args.n or 150)) if dim == 3 else ("steady2d_n%d" % (args.n or 50))
+    return dict(times=times, infos=infos, kern_ms=[o[0]["time_ms"] for o in outs],
+                kern_bytes=[o[0]["bytes_algo"] for o in outs], units_per_step=1, e2e=e2e,
+                h2d=hbytes + ch.numel() * 8, d2h=ch.numel() * 8, clocks=clocks, launches=launches,
+                config={"workload": name, "nodes": spec.n_nodes, "free": desc.get("n_free"),
+                        "nnz_free": desc.get("nnz_free"), "rtol": args.rtol, "solver": args.solver,
+                        "precision": args.precision, "l2": "flushed between steps (256 MB write)"},
+                dtype="f64" if prec == P.NN_PREC_FP64 else "f32+f64", unit="QP solves/s", metric="QP solves/s")
+
+
+def run_batch(P, torch, args, rank):
+    count = args.count
+    insts = I.config4_batch(count)
+    dev = torch.device("cuda")
+    prec = P.NN_PREC_MIXED if args.precision == "mixed" else P.NN_PREC_FP64
+    systems = [P.nn_assemble(P.Problem(sp, device=dev)) for sp in insts]
+    cs = [torch.zeros(sp.n_nodes, dtype=torch.float64, device=dev) for sp in insts]
+    opts = P.solve_opts(rtol=args.rtol, precision=prec)
+    tuned = P.nn_batch_autotune(systems, opts)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def step():
+        for c in cs:
+            c.zero_()
+        return P.nn_batch_solve(systems, cs, opts)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    l0 = P.kernel_launches()
+    times, outs, clocks = timed_steps(torch, step, args.steps, flush,
+                                      ClockSampler(os.path.join(args.out_dir, "clocks_rank%d.csv" % rank)))
+    launches = P.kernel_launches() - l0
+    infos = [i for o in outs for i in o]
+    return dict(times=times, infos=infos, kern_ms=[o[0]["time_ms"] for o in outs],
+                kern_bytes=[sum(i["bytes_algo"] for i in o) for o in outs], units_per_step=count, e2e=None,
+                h2d=0, d2h=0, clocks=clocks, launches=launches,
+                config={"workload": "batch2d_%d" % count, "instances": count, "threads_per_block": tuned,
+                        "precision": args.precision, "rtol": args.rtol, "l2": "flushed between steps"},
+                dtype="f64" if prec == P.NN_PREC_FP64 else "f32+f64", unit="QP solves/s", metric="QP solves/s")
+
+
+def run_serve(P, torch, args, rank):
+    rate, duration = args.rate, args.duration
+    arrivals = I.serve_arrivals(rate, duration)
+    pool = [I.serve_request(r) for r in range(args.pool)]
+    probs = [P.Problem(sp) for sp in pool]
+    budget = int(args.budget_gb * (1 << 30))
+    sv = P.nn_serve_create(budget, P.serve_opts(max_inflight=args.inflight))
+    # warm-up: one request of each kind
+    for k in range(min(2, len(probs))):
+        rid = P.nn_serve_submit(sv, probs[k])
+        P.nn_serve_drain(sv)
+        P.nn_serve_poll(sv, rid, np.zeros(pool[k].n_nodes))
+    P.nn_serve_destroy(sv)
+    sv = P.nn_serve_create(budget, P.serve_opts(max_inflight=args.inflight))
+    l0 = P.kernel_launches()
+    ids = []
+    t0 = time.perf_counter()
+    for k, ta in enumerate(arrivals):
+        now = time.perf_counter() - t0
+        if ta > now:
+            time.sleep(ta - now)
+        try:
+            ids.append((P.nn_serve_submit(sv, probs[k % len(probs)]), k % len(probs)))
+        except P.NnError:
+            pass
+    P.nn_serve_drain(sv)
+    wall = time.perf_counter() - t0
+    st = P.nn_serve_stats(sv)
+    ok = 0
+    for rid, k in ids:
+        info = P.nn_serve_poll(sv, rid, np.zeros(pool[k].n_nodes))
+        ok += info is not None and info["status"] == 0
+    P.nn_serve_destroy(sv)
+    launches = P.kernel_launches() - l0
+    return dict(stats=st, wall=wall, offered=len(arrivals), ok=ok, launches=launches,
+                config={"workload": "serve_poisson%g_for%gs" % (rate, duration), "payload_pool": args.pool,
+                        "max_inflight": args.inflight, "budget_gb": args.budget_gb})
 
 
 def main():
@@ -240,8 +398,19 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="transient3d")
+    ap.add_argument("--workload", default="transient3d",
+                    choices=["transient3d", "steady3d", "steady2d", "batch", "serve"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--solver", default="gpcg", choices=["gpcg", "lbfgs"])
+    ap.add_argument("--n", type=int, default=0)
+    ap.add_argument("--count", type=int, default=512)
     ap.add_argument("--rtol", type=float, default=1e-10)
+    ap.add_argument("--max-iter", type=int, default=200000)
+    ap.add_argument("--rate", type=float, default=200.0)
+    ap.add_argument("--duration", type=float, default=10.0)
+    ap.add_argument("--pool", type=int, default=64)
+    ap.add_argument("--inflight", type=int, default=8)
+    ap.add_argument("--budget-gb", type=float, default=120.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--out-dir", default=os.path.join(ROOT, "gpurun_out"))
     args = ap.parse_args()
@@ -249,29 +418,28 @@ def main():
     dist, rank, ws = dist_init()
     pk = peaks()
     hbm_peak = pk["hbm_gbs"] if pk else FALLBACK_HBM
-    peak_src = "measured" if pk else "fallback"
+    peak_src = "measured (MEASURED_PEAKS.json hbm_gbs)" if pk else "fallback"
 
     if args.impl == "reference":
         if rank != 0:
             return 0
-        vals = []
-        cores, desc = os.cpu_count() or 1, ""
+        vals, cores, desc = [], os.cpu_count() or 1, ""
         t0 = time.perf_counter()
         for _ in range(args.warmup):
-            oracle_sample(args.workload, budget_s=2.0)
+            oracle_sample(args.workload, budget_s=1.0)
         for _ in range(args.steps):
-            v, cores, desc = oracle_sample(args.workload, budget_s=10.0)
+            v, cores, desc = oracle_sample(args.workload, budget_s=8.0)
             vals.append(v)
         v = float(np.median(vals))
-        line = {"impl": "reference", "metric": "QP solves/s", "value": v, "unit": "QP solves/s",
-                "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": args.workload},
-                "cpu_baseline": {"value": v, "unit": "QP solves/s", "cores": cores, "kind": "oracle",
-                                 "sample": desc},
-                "e2e": {"value": v, "unit": "QP solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-                "wall_s": time.perf_counter() - t0}
-        print(json.dumps(line))
+        print(json.dumps({"impl": "reference", "metric": "QP solves/s", "value": v, "unit": "QP solves/s",
+                          "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                          "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                          "data": "synthetic", "config": {"workload": args.workload},
+                          "cpu_baseline": {"value": v, "unit": "QP solves/s", "cores": cores, "kind": "oracle",
+                                           "sample": desc},
+                          "e2e": {"value": v, "unit": "QP solves/s", "h2d_bytes_per_step": 0,
+                                  "d2h_bytes_per_step": 0},
+                          "wall_s": time.perf_counter() - t0}))
         return 0
 
     import torch
@@ -281,42 +449,63 @@ def main():
         return 1
     P.lib()
     barrier(dist)
-    if args.workload != "transient3d":
-        raise SystemExit("workload %s is run by bench_extra" % args.workload)
-    r = run_transient(P, torch, args, rank)
+    if args.workload == "serve":
+        r = run_serve(P, torch, args, rank)
+        st = r["stats"]
+        if rank == 0:
+            print(json.dumps({"metric": "serving p50/p99 latency", "value": st["p50_ms"], "unit": "ms",
+                              "p99_ms": st["p99_ms"], "mean_ms": st["mean_ms"], "solves_per_s": st["solves_per_s"],
+                              "offered": r["offered"], "offered_per_s": args.rate, "completed": st["completed"],
+                              "ok": r["ok"], "failed": st["failed"], "rejected": st["rejected"],
+                              "wall_s": r["wall"], "saturated": st["solves_per_s"] < 0.95 * args.rate,
+                              "bytes_peak": st["bytes_peak"], "inflight_peak": st["inflight_peak"],
+                              "higher_is_better": False, "n_gpus": ws, "dtype": "f64", "data": "synthetic",
+                              "gpu_launches": r["launches"], "config": r["config"]}))
+        return 0
+    if args.workload == "transient3d":
+        r = run_transient(P, torch, args, rank)
+    elif args.workload == "steady3d":
+        r = run_steady(P, torch, args, rank, 3)
+    elif args.workload == "steady2d":
+        r = run_steady(P, torch, args, rank, 2)
+    else:
+        r = run_batch(P, torch, args, rank)
     barrier(dist)
     total_ms = max_over_ranks(dist, sum(r["times"]))
     units = r["units_per_step"] * args.steps * ws
     value = units / (total_ms / 1e3)
-    e2e_ms = max_over_ranks(dist, sum(r["e2e"]))
-    e2e_val = r["units_per_step"] * len(r["e2e"]) * ws / (e2e_ms / 1e3)
     kern_ms = float(np.mean(r["kern_ms"]))
     kern_bytes = float(np.mean(r["kern_bytes"]))
     achieved = kern_bytes / (kern_ms / 1e3) / 1e9
+    tfile = os.path.join(ROOT, "profiles", "traffic_%s.json" % r["config"]["workload"])
     traffic = None
-    tfile = os.path.join(ROOT, "profiles", "transient3d_traffic.json")
     if os.path.exists(tfile):
         try:
             traffic = json.load(open(tfile)).get("dram_bytes_per_launch")
         except Exception:
             traffic = None
-    line = {"metric": "QP solves/s", "value": value, "unit": "QP solves/s", "n_gpus": ws, "steps": args.steps,
+    infos = r["infos"]
+    line = {"metric": r["metric"], "value": value, "unit": r["unit"], "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": r["dtype"], "data": "synthetic", "config": r["config"],
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                          "frac": achieved / hbm_peak, "traffic": traffic,
-                         "kernel": "k_solve_grid (persistent GPCG, 50 steps per launch)",
+                         "kernel": "solve kernel (persistent, one launch per step)",
                          "kernel_ms": kern_ms, "algo_bytes_per_launch": kern_bytes, "peak_source": peak_src},
-            "e2e": {"value": e2e_val, "unit": "QP solves/s", "h2d_bytes_per_step": r["h2d"],
-                    "d2h_bytes_per_step": r["d2h"]},
-            "gpu_launches": r["launches"],
-            "clocks": r["clocks"],
-            "max_kkt_rel": float(max(r["kkt"])),
-            "statuses_ok": all(s == 0 for s in r["statuses"]),
-            "spmv_per_step": r["spmv"] / args.steps}
+            "gpu_launches": r["launches"], "clocks": r["clocks"],
+            "max_kkt_rel": float(max(i["kkt_rel"] for i in infos)),
+            "statuses_ok": all(i["status"] == 0 for i in infos),
+            "spmv_per_step": sum(i["spmv"] for i in infos) / args.steps}
+    if r["e2e"] is not None:
+        e2e_ms = max_over_ranks(dist, sum(r["e2e"]))
+        line["e2e"] = {"value": r["units_per_step"] * len(r["e2e"]) * ws / (e2e_ms / 1e3), "unit": r["unit"],
+                       "h2d_bytes_per_step": r["h2d"], "d2h_bytes_per_step": r["d2h"]}
+    else:
+        line["e2e"] = None
     if rank == 0 and not args.no_cpu_baseline:
-        v, cores, desc = oracle_sample("transient3d")
-        line["cpu_baseline"] = {"value": v, "unit": "QP solves/s", "cores": cores, "kind": "oracle", "sample": desc}
+        v, cores, desc = oracle_sample(args.workload)
+        if v is not None:
+            line["cpu_baseline"] = {"value": v, "unit": r["unit"], "cores": cores, "kind": "oracle", "sample": desc}
     if rank == 0:
         print(json.dumps(line))
     if dist is not None:

@@ -195,6 +195,8 @@ typedef struct {
     double time_ms;      /* device time of the call (CUDA events) */
     double bytes_algo;   /* algorithmic bytes moved (perfect-cache model) */
     int64_t active_lo, active_hi; /* entries exactly at lo / hi */
+    int64_t fp64_fallback; /* mixed: 1 if refinement stopped contracting and the solve
+                              finished with FP64 iterations (the result still meets rtol) */
 } nn_solve_info;
 
 /* Solves the steady QP  min 1/2 x'Ax - x'b0, lo <= x <= hi  over the free

@@ -76,7 +76,7 @@ class nn_solve_info(ctypes.Structure):
     _fields_ = [("status", c_int), ("iterations", c_int64), ("spmv", c_int64), ("spmv64", c_int64),
                 ("cg_iters", c_int64), ("refinements", c_int64), ("kkt_rel", c_double), ("kkt_inf", c_double),
                 ("objective", c_double), ("time_ms", c_double), ("bytes_algo", c_double),
-                ("active_lo", c_int64), ("active_hi", c_int64)]
+                ("active_lo", c_int64), ("active_hi", c_int64), ("fp64_fallback", c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

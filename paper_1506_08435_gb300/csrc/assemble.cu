@@ -20,6 +20,7 @@
 #include <algorithm>
 #include "internal.h"
 #include "scan.cuh"
+#include "ops.cuh"
 
 namespace nnqp {
 
@@ -416,7 +417,7 @@ __global__ void k_slice_width(int64_t NF, int64_t nslices, const int64_t *offcnt
         int64_t i = s * 32 + l;
         if (i < NF && offcnt[i] > w) w = offcnt[i];
     }
-    wslots[s] = 32 * w;
+    wslots[s] = 32 * (w + (w & 1));   // even width: entries are stored in pairs
 }
 
 // One thread per slot row: writes the row's off-diagonals into its SELL
@@ -427,15 +428,17 @@ __global__ void k_sell_fill(int64_t NF, int64_t nslices, const int64_t *arow, co
                             float *dinv32, double *dinv64, const double *diag) {
     int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t >= nslices * 32) return;
-    const int64_t s = t >> 5, lane = t & 31;
+    const int64_t s = t >> 5;
+    const int lane = (int)(t & 31);
     const int64_t base = sptr[s];
     const int w = (int)((sptr[s + 1] - base) >> 5);
     if (t >= NF) {
         for (int k = 0; k < w; ++k) {
-            scol[base + 32 * k + lane] = 0;
-            sval[base + 32 * k + lane] = 0.0;
-            if (sval32) sval32[base + 32 * k + lane] = 0.0f;
-            if (smval) smval[base + 32 * k + lane] = 0.0;
+            const int64_t idx = sell_idx(base, k, lane);
+            scol[idx] = 0;
+            sval[idx] = 0.0;
+            if (sval32) sval32[idx] = 0.0f;
+            if (smval) smval[idx] = 0.0;
         }
         return;
     }
@@ -443,7 +446,7 @@ __global__ void k_sell_fill(int64_t NF, int64_t nslices, const int64_t *arow, co
     double off32sum = 0.0;
     for (int64_t q = arow[t]; q < arow[t + 1]; ++q) {
         if (acol[q] == t) continue;
-        const int64_t idx = base + 32 * k + lane;
+        const int64_t idx = sell_idx(base, k, lane);
         scol[idx] = acol[q];
         sval[idx] = aval[q];
         if (sval32) {
@@ -455,7 +458,7 @@ __global__ void k_sell_fill(int64_t NF, int64_t nslices, const int64_t *arow, co
         ++k;
     }
     for (; k < w; ++k) {
-        const int64_t idx = base + 32 * k + lane;
+        const int64_t idx = sell_idx(base, k, lane);
         scol[idx] = (int32_t)t;
         sval[idx] = 0.0;
         if (sval32) sval32[idx] = 0.0f;

@@ -36,7 +36,7 @@ struct BatchInst {
     float *w32;         // 12 n floats (mixed)
 };
 
-constexpr int kBatchCounters = 8;
+constexpr int kBatchCounters = 9;
 
 template <int TPB, int MIXED>
 __global__ void __launch_bounds__(TPB) k_batch(const BatchInst *__restrict__ insts, const int *__restrict__ order,
@@ -67,9 +67,12 @@ __global__ void __launch_bounds__(TPB) k_batch(const BatchInst *__restrict__ ins
             GpcgVecs<float> v{w, w + n, w + 2 * n, w + 3 * n, w + 4 * n, w + 5 * n, w + 6 * n, w + 7 * n, w + 8 * n,
                               w + 9 * n, I.dinv32};
             const SellF32Diff A32{n, I.nslices, I.sptr, I.col, I.val32, I.rsum32};
+            double *w6 = I.w64;
+            GpcgVecs<double> v64{x, w6 + n, w6 + 2 * n, w6 + 3 * n, w6 + 4 * n, w6 + 5 * n, w6 + 6 * n,
+                                 w6 + 7 * n, w6 + 8 * n, I.b0, I.dinv64};
             MixedStats ms;
-            status = mixed_solve(T, R, A, A32, I.lo, I.hi, I.b0, x, v, w + 9 * n, w + 10 * n, w + 11 * n,
-                                 rtol * I.den, inner_rtol, max_ref, ctl.max_spmv, ctl, ms);
+            status = mixed_solve(T, R, A, A32, I.lo, I.hi, I.b0, x, v, w + 9 * n, w + 10 * n, w + 11 * n, v64,
+                                 rtol * I.den, inner_rtol, max_ref, ctl.max_spmv, ctl, ctl, ms);
             cnt[1] = ms.spmv64;
             cnt[2] = ms.spmv32;
             cnt[3] = ms.cg;
@@ -77,6 +80,7 @@ __global__ void __launch_bounds__(TPB) k_batch(const BatchInst *__restrict__ ins
             cnt[5] = ms.refinements;
             cnt[6] = ms.vec64;
             cnt[7] = ms.vec32;
+            cnt[8] = ms.fallback;
             gp2 = ms.gp2;
         } else {
             double *w = I.w64;
@@ -239,7 +243,11 @@ static nn_status run_batch(int count, nn_system *const *systems, double *const *
     ctl.eta2 = 1e-3;
     ctl.mu = 1e-4;
     ctl.cg_variant = 0;
+    ctl.cg_bound_stop = 0;
     if (const char *e = getenv("NNQP_BATCH_CG_VARIANT")) ctl.cg_variant = atoi(e);
+    if (const char *e = getenv("NNQP_CG_BOUND_STOP")) ctl.cg_bound_stop = atoi(e);
+    if (const char *e = getenv("NNQP_GP_MAX")) ctl.gp_max = atoi(e);
+    if (const char *e = getenv("NNQP_ETA2")) ctl.eta2 = atof(e);
     BatchKernel k = pick(tpb, mixed);
     int per = 0, dev = 0, sms = 0;
     cudaGetDevice(&dev);
@@ -275,6 +283,7 @@ static nn_status run_batch(int count, nn_system *const *systems, double *const *
         inf.cg_iters = q[3];
         inf.iterations = q[4];
         inf.refinements = q[5];
+        inf.fp64_fallback = q[8];
         inf.kkt_rel = std::sqrt(hs[2 * i]) / hs[2 * i + 1];
         inf.kkt_inf = NAN;
         inf.objective = NAN;

@@ -3,22 +3,26 @@
 // (the non-negative formulation, Sec. 2.1.3, and its transient form with
 // c_min, c_max, Sec. 2.2.2; GPCG is the TAO method named in Sec. 3.1).
 // Algorithm after More & Toraldo (SIAM J. Optim. 1, 1991):
-//   * gradient-projection phase: steepest descent along -gP with the Cauchy
-//     step length, projected onto the box, backtracking until the Armijo
-//     condition q(w) - q(x) <= mu g'(w - x) holds; repeated until the
-//     active set stops changing or the decrease stalls (eta1);
+//   * gradient-projection phase: projected steps x <- P(x - alpha gP) with
+//     the Cauchy length first and Barzilai-Borwein lengths afterwards,
+//     backtracking until the Armijo condition q(w) - q(x) <= mu g'(w - x)
+//     holds; repeated until the active set stops changing or the decrease
+//     stalls (eta1);
 //   * CG phase: Jacobi-preconditioned CG on the face {l < x < h} with the
-//     active entries frozen, stopped when the face residual is small, a
-//     bound is crossed, or the decrease per iteration stalls (eta2); then a
-//     projected search along the CG step.  If every active entry is
-//     binding (its projected gradient is zero) the next phase is CG on the
-//     new face, else gradient projection.
+//     active entries frozen, run until the face residual is small or the
+//     decrease per iteration stalls (eta2); then a projected search along the
+//     CG step, which clips entries that crossed a bound.  If every active
+//     entry is binding (its projected gradient is zero) the next phase is CG
+//     on the new face, else gradient projection.
 // Objective differences use q(w) - q(x) = 1/2 (g(x) + g(w))'(w - x), exact
 // for a quadratic, so no large objective values are subtracted.
 //
 // Every vector pass is over the rows owned by the calling thread (Rows);
 // passes are separated by team barriers; every scalar comes out of a team
-// reduction, so all threads take the same branches.
+// reduction, so all threads take the same branches.  Per-thread partial sums
+// are kept in the vector type V (FP32 in the mixed-precision inner solves,
+// where FP64 arithmetic would cost 59x more per operation) and enter the
+// FP64 team reduction once per pass.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -59,6 +63,14 @@ __device__ __forceinline__ V proj_grad(V x, V g, V l, V h) {
     return g;
 }
 
+// Team reduction of per-thread partials kept in V.
+template <class Team, typename V, int K>
+__device__ __forceinline__ bool team_sum(Team &T, const V (&acc)[K], double (&out)[K]) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) out[k] = (double)acc[k];
+    return T.reduce(out);
+}
+
 template <typename V>
 struct GpcgVecs {
     V *x, *g, *p, *q, *r, *z, *s, *w, *gw;
@@ -76,6 +88,8 @@ struct GpcgCtl {
     double mu;           // Armijo constant
     int cg_variant;      // 0: textbook PCG (3 team barriers per iteration);
                          // 1: Chronopoulos-Gear PCG (2 barriers, one fused reduction)
+    int cg_bound_stop;   // 1: end the CG phase as soon as x + s leaves the box;
+                         // 0: run CG to its stall test, the projected search clips
 };
 
 // vec counts vector streams (one read or write of an n-vector) made by the
@@ -92,23 +106,26 @@ template <class Team, class Op, typename V>
 __device__ int gpcg_solve(Team &T, const Rows &R, const Op &A, const Bounds<V> &B, GpcgVecs<V> &v,
                           const GpcgCtl &C, GpcgStats &st) {
     const double tol2 = C.tol * C.tol, ftol2 = C.face_tol * C.face_tol;
+    const V zero = (V)0, one = (V)1;
     R.each([&](int64_t i) { v.x[i] = clampv(v.x[i], B.l(i), B.h(i)); });
     st.vec += 2;
     if (!T.sync()) return ST_TIMEOUT;
     {
-        double a[1] = {0.0};
+        V a[1] = {zero};
+        double d[1];
         A.apply(R, v.x, [&](int64_t i, V ax) {
             V gi = ax - v.b[i];
             v.g[i] = gi;
             V gp = proj_grad(v.x[i], gi, B.l(i), B.h(i));
-            a[0] += (double)gp * (double)gp;
+            a[0] += gp * gp;
         });
-        if (!T.reduce(a)) return ST_TIMEOUT;
+        if (!team_sum(T, a, d)) return ST_TIMEOUT;
         ++st.spmv;
         st.vec += 1;
-        st.gp2 = a[0];
+        st.gp2 = d[0];
     }
     int status = ST_NOT_CONVERGED;
+    double bb = 0.0;   // step length carried between gradient-projection steps
     for (;;) {
         if (!isfinite(st.gp2)) { status = ST_NUMERIC; break; }
         if (st.gp2 <= tol2) { status = ST_OK; break; }
@@ -117,53 +134,64 @@ __device__ int gpcg_solve(Team &T, const Rows &R, const Op &A, const Bounds<V> &
         // ------------------------------------------------ gradient projection
         double maxdec = 0.0;
         for (int it = 0; it < C.gp_max; ++it) {
-            R.each([&](int64_t i) { v.p[i] = -proj_grad(v.x[i], v.g[i], B.l(i), B.h(i)); });
-            st.vec += 3;
-            if (!T.sync()) return ST_TIMEOUT;
-            double a1[1] = {0.0};
-            A.apply(R, v.p, [&](int64_t i, V ap) { a1[0] += (double)v.p[i] * (double)ap; });
-            if (!T.reduce(a1)) return ST_TIMEOUT;
-            ++st.spmv;
-            if (!(a1[0] > 0.0)) break;
-            double alpha = st.gp2 / a1[0];
+            double alpha = bb;
+            if (!(alpha > 0.0)) {   // Cauchy length along -gP
+                R.each([&](int64_t i) { v.p[i] = -proj_grad(v.x[i], v.g[i], B.l(i), B.h(i)); });
+                st.vec += 3;
+                if (!T.sync()) return ST_TIMEOUT;
+                V a1[1] = {zero};
+                double d1[1];
+                A.apply(R, v.p, [&](int64_t i, V ap) { a1[0] += v.p[i] * ap; });
+                if (!team_sum(T, a1, d1)) return ST_TIMEOUT;
+                ++st.spmv;
+                if (!(d1[0] > 0.0)) break;
+                alpha = st.gp2 / d1[0];
+            }
             bool accepted = false;
-            double a2[4];
+            double d2[6];
             for (int ls = 0; ls < 48 && st.spmv < C.max_spmv; ++ls) {
-                a2[0] = a2[1] = a2[2] = a2[3] = 0.0;
+                V a2[6] = {zero, zero, zero, zero, zero, zero};
                 const V va = (V)alpha;
                 R.each([&](int64_t i) {
                     V l = B.l(i), h = B.h(i), xi = v.x[i];
-                    V wi = clampv(xi + va * v.p[i], l, h);
+                    V wi = clampv(xi - va * proj_grad(xi, v.g[i], l, h), l, h);
                     v.w[i] = wi;
-                    a2[0] += (double)v.g[i] * (double)(wi - xi);
-                    a2[1] += ((xi <= l || xi >= h) != (wi <= l || wi >= h)) ? 1.0 : 0.0;
+                    a2[0] += v.g[i] * (wi - xi);
+                    a2[1] += ((xi <= l || xi >= h) != (wi <= l || wi >= h)) ? one : zero;
                 });
                 if (!T.sync()) return ST_TIMEOUT;
                 A.apply(R, v.w, [&](int64_t i, V aw) {
                     V gwi = aw - v.b[i];
                     v.gw[i] = gwi;
                     V wi = v.w[i];
-                    a2[2] += (double)(v.g[i] + gwi) * (double)(wi - v.x[i]);
+                    V si = wi - v.x[i], yi = gwi - v.g[i];
+                    a2[2] += (v.g[i] + gwi) * si;
                     V gp = proj_grad(wi, gwi, B.l(i), B.h(i));
-                    a2[3] += (double)gp * (double)gp;
+                    a2[3] += gp * gp;
+                    a2[4] += si * si;
+                    a2[5] += si * yi;
                 });
-                if (!T.reduce(a2)) return ST_TIMEOUT;
+                if (!team_sum(T, a2, d2)) return ST_TIMEOUT;
                 ++st.spmv;
                 st.vec += 7;
-                if (0.5 * a2[2] <= C.mu * a2[0]) {
+                if (0.5 * d2[2] <= C.mu * d2[0]) {
                     accepted = true;
                     break;
                 }
                 alpha *= 0.5;
             }
-            if (!accepted) break;
+            if (!accepted) {
+                bb = 0.0;
+                break;
+            }
             V *t = v.x; v.x = v.w; v.w = t;
             t = v.g; v.g = v.gw; v.gw = t;
-            st.gp2 = a2[3];
-            double dec = -0.5 * a2[2];
+            st.gp2 = d2[3];
+            bb = d2[5] > 0.0 ? d2[4] / d2[5] : 0.0;
+            const double dec = -0.5 * d2[2];
             if (dec > maxdec) maxdec = dec;
             if (st.gp2 <= tol2 || st.spmv >= C.max_spmv) break;
-            if (a2[1] == 0.0 || dec <= C.eta1 * maxdec) break;
+            if (d2[1] == 0.0 || dec <= C.eta1 * maxdec) break;
         }
         if (st.gp2 <= tol2 || st.spmv >= C.max_spmv || !isfinite(st.gp2)) continue;
         // ------------------------------------------------ CG on faces
@@ -175,33 +203,35 @@ __device__ int gpcg_solve(Team &T, const Rows &R, const Op &A, const Bounds<V> &
                 R.each([&](int64_t i) {
                     V xi = v.x[i];
                     bool fr = xi > B.l(i) && xi < B.h(i);
-                    V ri = fr ? -v.g[i] : (V)0;
+                    V ri = fr ? -v.g[i] : zero;
                     v.r[i] = ri;
                     v.z[i] = v.dinv[i] * ri;
-                    v.s[i] = (V)0;
-                    v.p[i] = (V)0;
-                    v.q[i] = (V)0;
+                    v.s[i] = zero;
+                    v.p[i] = zero;
+                    v.q[i] = zero;
                 });
                 st.vec += 8;
                 if (!T.sync()) return ST_TIMEOUT;
-                double c3[4] = {0.0, 0.0, 0.0, 0.0};   // gamma, delta, r'r, bound crossings
+                V a3[2] = {zero, zero};
+                double d3[2];
                 A.apply(R, v.z, [&](int64_t i, V au) {
                     V xi = v.x[i];
-                    V wi = (xi > B.l(i) && xi < B.h(i)) ? au : (V)0;
+                    V wi = (xi > B.l(i) && xi < B.h(i)) ? au : zero;
                     v.w[i] = wi;
-                    V ri = v.r[i];
-                    c3[0] += (double)ri * (double)v.z[i];
-                    c3[1] += (double)wi * (double)v.z[i];
+                    V ui = v.z[i];
+                    a3[0] += v.r[i] * ui;
+                    a3[1] += wi * ui;
                 });
-                if (!T.reduce(c3)) return ST_TIMEOUT;
+                if (!team_sum(T, a3, d3)) return ST_TIMEOUT;
                 ++st.spmv;
                 st.vec += 3;
-                double gamma = c3[0], delta = c3[1];
+                double gamma = d3[0], delta = d3[1];
                 if (!(gamma > 0.0) || !(delta > 0.0)) break;
                 double alpha = gamma / delta, beta = 0.0, maxdec = 0.0;
                 for (int k = 0; k < C.cg_max; ++k) {
                     const V va = (V)alpha, vb = (V)beta;
-                    double c4[4] = {0.0, 0.0, 0.0, 0.0};
+                    V a4[4] = {zero, zero, zero, zero};   // gamma, delta, r'r, bound crossings
+                    double d4[4];
                     R.each([&](int64_t i) {
                         V pi = v.z[i] + vb * v.p[i];
                         V qi = v.w[i] + vb * v.q[i];
@@ -213,122 +243,126 @@ __device__ int gpcg_solve(Team &T, const Rows &R, const Op &A, const Bounds<V> &
                         v.r[i] = ri;
                         v.z[i] = v.dinv[i] * ri;
                         V xs = v.x[i] + si;
-                        c4[3] += (xs < B.l(i) || xs > B.h(i)) ? 1.0 : 0.0;
+                        a4[3] += (xs < B.l(i) || xs > B.h(i)) ? one : zero;
                     });
                     st.vec += 13;
                     if (!T.sync()) return ST_TIMEOUT;
                     A.apply(R, v.z, [&](int64_t i, V au) {
                         V xi = v.x[i];
-                        V wi = (xi > B.l(i) && xi < B.h(i)) ? au : (V)0;
+                        V wi = (xi > B.l(i) && xi < B.h(i)) ? au : zero;
                         v.w[i] = wi;
                         V ri = v.r[i], ui = v.z[i];
-                        c4[0] += (double)ri * (double)ui;
-                        c4[1] += (double)wi * (double)ui;
-                        c4[2] += (double)ri * (double)ri;
+                        a4[0] += ri * ui;
+                        a4[1] += wi * ui;
+                        a4[2] += ri * ri;
                     });
-                    if (!T.reduce(c4)) return ST_TIMEOUT;
+                    if (!team_sum(T, a4, d4)) return ST_TIMEOUT;
                     ++st.spmv;
                     ++st.cg;
                     st.vec += 3;
                     const double dec = 0.5 * alpha * gamma;
                     if (dec > maxdec) maxdec = dec;
-                    const double gnew = c4[0];
-                    if (c4[3] > 0.0 || dec <= C.eta2 * maxdec || c4[2] <= ftol2 || st.spmv >= C.max_spmv ||
-                        !(gnew > 0.0))
+                    const double gnew = d4[0];
+                    if ((C.cg_bound_stop && d4[3] > 0.0) || dec <= C.eta2 * maxdec || d4[2] <= ftol2 ||
+                        st.spmv >= C.max_spmv || !(gnew > 0.0))
                         break;
                     beta = gnew / gamma;
-                    const double den = c4[1] - beta * gnew / alpha;
+                    const double den = d4[1] - beta * gnew / alpha;
                     if (!(den > 0.0)) break;
                     alpha = gnew / den;
                     gamma = gnew;
                 }
             } else {
-            double a3[1] = {0.0};
-            R.each([&](int64_t i) {
-                V xi = v.x[i];
-                bool fr = xi > B.l(i) && xi < B.h(i);
-                V ri = fr ? -v.g[i] : (V)0;
-                V zi = v.dinv[i] * ri;
-                v.r[i] = ri;
-                v.z[i] = zi;
-                v.p[i] = zi;
-                v.s[i] = (V)0;
-                a3[0] += (double)ri * (double)zi;
-            });
-            if (!T.reduce(a3)) return ST_TIMEOUT;
-            st.vec += 7;
-            double rho = a3[0];
-            if (!(rho > 0.0)) break;
-            double maxdec = 0.0;
-            for (int k = 0; k < C.cg_max; ++k) {
-                double a4[1] = {0.0};
-                A.apply(R, v.p, [&](int64_t i, V ap) {
-                    V xi = v.x[i];
-                    V qi = (xi > B.l(i) && xi < B.h(i)) ? ap : (V)0;
-                    v.q[i] = qi;
-                    a4[0] += (double)v.p[i] * (double)qi;
-                });
-                if (!T.reduce(a4)) return ST_TIMEOUT;
-                ++st.spmv;
-                st.vec += 1;
-                if (!(a4[0] > 0.0)) break;
-                const double alpha = rho / a4[0];
-                const V va = (V)alpha;
-                double a5[3] = {0.0, 0.0, 0.0};
+                // textbook preconditioned CG
+                V a3[1] = {zero};
+                double d3[1];
                 R.each([&](int64_t i) {
-                    V si = v.s[i] + va * v.p[i];
-                    V ri = v.r[i] - va * v.q[i];
+                    V xi = v.x[i];
+                    bool fr = xi > B.l(i) && xi < B.h(i);
+                    V ri = fr ? -v.g[i] : zero;
                     V zi = v.dinv[i] * ri;
-                    v.s[i] = si;
                     v.r[i] = ri;
                     v.z[i] = zi;
-                    a5[0] += (double)ri * (double)zi;
-                    a5[1] += (double)ri * (double)ri;
-                    V xs = v.x[i] + si;
-                    a5[2] += (xs < B.l(i) || xs > B.h(i)) ? 1.0 : 0.0;
+                    v.p[i] = zi;
+                    v.s[i] = zero;
+                    a3[0] += ri * zi;
                 });
-                if (!T.reduce(a5)) return ST_TIMEOUT;
-                ++st.cg;
-                st.vec += 9;
-                const double dec = 0.5 * alpha * rho;
-                if (dec > maxdec) maxdec = dec;
-                if (a5[2] > 0.0 || dec <= C.eta2 * maxdec || a5[1] <= ftol2 || st.spmv >= C.max_spmv ||
-                    !(a5[0] > 0.0))
-                    break;
-                const V vb = (V)(a5[0] / rho);
-                rho = a5[0];
-                R.each([&](int64_t i) { v.p[i] = v.z[i] + vb * v.p[i]; });
-                st.vec += 3;
-                if (!T.sync()) return ST_TIMEOUT;
+                if (!team_sum(T, a3, d3)) return ST_TIMEOUT;
+                st.vec += 7;
+                double rho = d3[0];
+                if (!(rho > 0.0)) break;
+                double maxdec = 0.0;
+                for (int k = 0; k < C.cg_max; ++k) {
+                    V a4[1] = {zero};
+                    double d4[1];
+                    A.apply(R, v.p, [&](int64_t i, V ap) {
+                        V xi = v.x[i];
+                        V qi = (xi > B.l(i) && xi < B.h(i)) ? ap : zero;
+                        v.q[i] = qi;
+                        a4[0] += v.p[i] * qi;
+                    });
+                    if (!team_sum(T, a4, d4)) return ST_TIMEOUT;
+                    ++st.spmv;
+                    st.vec += 1;
+                    if (!(d4[0] > 0.0)) break;
+                    const double alpha = rho / d4[0];
+                    const V va = (V)alpha;
+                    V a5[3] = {zero, zero, zero};
+                    double d5[3];
+                    R.each([&](int64_t i) {
+                        V si = v.s[i] + va * v.p[i];
+                        V ri = v.r[i] - va * v.q[i];
+                        V zi = v.dinv[i] * ri;
+                        v.s[i] = si;
+                        v.r[i] = ri;
+                        v.z[i] = zi;
+                        a5[0] += ri * zi;
+                        a5[1] += ri * ri;
+                        V xs = v.x[i] + si;
+                        a5[2] += (xs < B.l(i) || xs > B.h(i)) ? one : zero;
+                    });
+                    if (!team_sum(T, a5, d5)) return ST_TIMEOUT;
+                    ++st.cg;
+                    st.vec += 9;
+                    const double dec = 0.5 * alpha * rho;
+                    if (dec > maxdec) maxdec = dec;
+                    if ((C.cg_bound_stop && d5[2] > 0.0) || dec <= C.eta2 * maxdec || d5[1] <= ftol2 ||
+                        st.spmv >= C.max_spmv || !(d5[0] > 0.0))
+                        break;
+                    const V vb = (V)(d5[0] / rho);
+                    rho = d5[0];
+                    R.each([&](int64_t i) { v.p[i] = v.z[i] + vb * v.p[i]; });
+                    st.vec += 3;
+                    if (!T.sync()) return ST_TIMEOUT;
+                }
             }
-            }  // CG variants
             // projected search along the CG step s
             double alpha = 1.0;
             bool accepted = false;
-            double a6[5];
+            double d6[5];
             for (int ls = 0; ls < 48; ++ls) {
-                a6[0] = a6[1] = a6[2] = a6[3] = a6[4] = 0.0;
+                V a6[5] = {zero, zero, zero, zero, zero};
                 const V va = (V)alpha;
                 R.each([&](int64_t i) {
                     V xi = v.x[i];
                     V wi = clampv(xi + va * v.s[i], B.l(i), B.h(i));
                     v.w[i] = wi;
-                    a6[0] += (double)v.g[i] * (double)(wi - xi);
+                    a6[0] += v.g[i] * (wi - xi);
                 });
                 if (!T.sync()) return ST_TIMEOUT;
                 A.apply(R, v.w, [&](int64_t i, V aw) {
                     V gwi = aw - v.b[i];
                     v.gw[i] = gwi;
                     V wi = v.w[i], l = B.l(i), h = B.h(i);
-                    a6[2] += (double)(v.g[i] + gwi) * (double)(wi - v.x[i]);
+                    a6[2] += (v.g[i] + gwi) * (wi - v.x[i]);
                     V gp = proj_grad(wi, gwi, l, h);
-                    a6[3] += (double)gp * (double)gp;
-                    a6[4] += ((wi <= l || wi >= h) && gp != (V)0) ? 1.0 : 0.0;
+                    a6[3] += gp * gp;
+                    a6[4] += ((wi <= l || wi >= h) && gp != zero) ? one : zero;
                 });
-                if (!T.reduce(a6)) return ST_TIMEOUT;
+                if (!team_sum(T, a6, d6)) return ST_TIMEOUT;
                 ++st.spmv;
                 st.vec += 7;
-                if (0.5 * a6[2] <= C.mu * a6[0]) {
+                if (0.5 * d6[2] <= C.mu * d6[0]) {
                     accepted = true;
                     break;
                 }
@@ -337,9 +371,9 @@ __device__ int gpcg_solve(Team &T, const Rows &R, const Op &A, const Bounds<V> &
             if (!accepted) break;
             V *t = v.x; v.x = v.w; v.w = t;
             t = v.g; v.g = v.gw; v.gw = t;
-            st.gp2 = a6[3];
+            st.gp2 = d6[3];
             if (st.gp2 <= tol2 || st.spmv >= C.max_spmv || !isfinite(st.gp2)) break;
-            if (a6[4] > 0.0) break;  // a non-binding active entry: back to gradient projection
+            if (d6[4] > 0.0) break;  // a non-binding active entry: back to gradient projection
         }
     }
     return status;

@@ -73,10 +73,12 @@ __device__ int lbfgs_solve(Team &T, const Rows &R, const Op &A, double lo, doubl
             double a[2 * kLbMaxM] = {0.0};
             R.each([&](int64_t i) {
                 const double gp = proj_grad(x[i], g[i], lo, hi);
-                for (int j = 0; j < k; ++j) {
-                    a[j] += S[(int64_t)ord[j] * n + i] * gp;
-                    a[kLbMaxM + j] += Y[(int64_t)ord[j] * n + i] * gp;
-                }
+#pragma unroll
+                for (int j = 0; j < kLbMaxM; ++j)
+                    if (j < k) {
+                        a[j] += S[(int64_t)ord[j] * n + i] * gp;
+                        a[kLbMaxM + j] += Y[(int64_t)ord[j] * n + i] * gp;
+                    }
             });
             if (!T.reduce(a)) return ST_TIMEOUT;
             st.vec += 2 + 2 * k;
@@ -96,9 +98,11 @@ __device__ int lbfgs_solve(Team &T, const Rows &R, const Op &A, double lo, doubl
             R.each([&](int64_t i) {
                 const double xi = x[i], gp = proj_grad(xi, g[i], lo, hi);
                 double hg = gamma * gp;
-                if (use_model)
-                    for (int j = 0; j < k; ++j)
-                        hg += sm.cs[j] * S[(int64_t)ord[j] * n + i] + sm.cy[j] * Y[(int64_t)ord[j] * n + i];
+                if (use_model) {
+#pragma unroll
+                    for (int j = 0; j < kLbMaxM; ++j)
+                        if (j < k) hg += sm.cs[j] * S[(int64_t)ord[j] * n + i] + sm.cy[j] * Y[(int64_t)ord[j] * n + i];
+                }
                 const bool binding = (xi <= lo || xi >= hi) && gp == 0.0;
                 const double di = binding ? 0.0 : -hg;
                 d[i] = di;
@@ -140,12 +144,14 @@ __device__ int lbfgs_solve(Team &T, const Rows &R, const Op &A, double lo, doubl
                 a[3] += si * yi;
                 a[4] += si * si;
                 a[5] += yi * yi;
-                for (int j = 0; j < k; ++j) {
-                    const double sj = S[(int64_t)ord[j] * n + i], yj = Y[(int64_t)ord[j] * n + i];
-                    a[6 + j] += si * yj;
-                    a[6 + kLbMaxM + j] += sj * yi;
-                    a[6 + 2 * kLbMaxM + j] += yi * yj;
-                }
+#pragma unroll
+                for (int j = 0; j < kLbMaxM; ++j)
+                    if (j < k) {
+                        const double sj = S[(int64_t)ord[j] * n + i], yj = Y[(int64_t)ord[j] * n + i];
+                        a[6 + j] += si * yj;
+                        a[6 + kLbMaxM + j] += sj * yi;
+                        a[6 + 2 * kLbMaxM + j] += yi * yj;
+                    }
             });
             if (!T.reduce(a)) return ST_TIMEOUT;
             ++st.spmv;

@@ -3,14 +3,25 @@
 // search direction, dot products) runs in the same pass over the rows.
 //
 // The product is the Hessian-vector product of the QP (the "MatMult" of the
-// paper's cost model, Sec. 4, Table of bytes transferred); the algorithmic
-// traffic of one product is nnz*(s_val + 4) + 4(n+1) + s_x n + s_y n.
+// paper's cost model, Sec. 4, Table 2); the algorithmic traffic of one
+// product is nnz*(s_val + 4) + 4(n+1) + s_x n + s_x n.
+//
+// SELL-32 layout with pair interleaving: in slice s (rows 32s..32s+31, width
+// w_s even), entry k of row 32s+l lives at
+//     sptr[s] + 64 (k/2) + 2 l + (k%2),
+// so lane l reads entries (k, k+1) of its row with one vector load: 16 bytes
+// for FP64 values, 8 bytes for column indices and FP32 values, and a warp
+// reads 512 (256) contiguous bytes per load instruction.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include "team.cuh"
 
 namespace nnqp {
+
+__host__ __device__ __forceinline__ int64_t sell_idx(int64_t base, int k, int lane) {
+    return base + 64 * (int64_t)(k >> 1) + 2 * lane + (k & 1);
+}
 
 // SELL-32, FP64 values; off-diagonals in slices, diagonal separate:
 //   y_i = d_i x_i + sum_k v_ik x_{c_ik}
@@ -21,6 +32,29 @@ struct SellF64 {
     const double *__restrict__ val;
     const double *__restrict__ diag;
 
+    template <typename VX>
+    __device__ __forceinline__ double row(int64_t s, int lane, int64_t base, int w, const VX *x) const {
+        const int2 *c2 = reinterpret_cast<const int2 *>(col + base) + lane;
+        const double2 *v2 = reinterpret_cast<const double2 *>(val + base) + lane;
+        double a0 = 0.0, a1 = 0.0;
+        int k = 0;
+        for (; k + 4 <= w; k += 4) {
+            const int2 ca = __ldg(c2 + 16 * k), cb = __ldg(c2 + 16 * k + 32);
+            const double2 va = __ldg(v2 + 16 * k), vb = __ldg(v2 + 16 * k + 32);
+            a0 = fma(va.x, (double)x[ca.x], a0);
+            a1 = fma(va.y, (double)x[ca.y], a1);
+            a0 = fma(vb.x, (double)x[cb.x], a0);
+            a1 = fma(vb.y, (double)x[cb.y], a1);
+        }
+        if (k < w) {
+            const int2 ca = __ldg(c2 + 16 * k);
+            const double2 va = __ldg(v2 + 16 * k);
+            a0 = fma(va.x, (double)x[ca.x], a0);
+            a1 = fma(va.y, (double)x[ca.y], a1);
+        }
+        return a0 + a1;
+    }
+
     template <class Epi>
     __device__ __forceinline__ void apply(const Rows &R, const double *x, Epi &&epi) const {
         const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
@@ -28,13 +62,20 @@ struct SellF64 {
             const int64_t base = __ldg(sptr + s);
             const int w = (int)((__ldg(sptr + s + 1) - base) >> 5);
             const int64_t i = s * 32 + lane;
-            const int32_t *c = col + base + lane;
-            const double *v = val + base + lane;
-            double acc = 0.0;
-#pragma unroll 4
-            for (int k = 0; k < w; ++k) acc = fma(__ldg(v + 32 * k), x[__ldg(c + 32 * k)], acc);
+            const double acc = row(s, lane, base, w, x);
             if (i < n) epi(i, fma(__ldg(diag + i), x[i], acc));
         }
+    }
+
+    // (A x)_i for one row (used outside the fused passes).
+    __device__ __forceinline__ double row_product(int64_t i, const double *x) const {
+        const int64_t s = i >> 5;
+        const int lane = (int)(i & 31);
+        const int64_t base = sptr[s];
+        const int w = (int)((sptr[s + 1] - base) >> 5);
+        double acc = 0.0;
+        for (int k = 0; k < w; ++k) acc = fma(val[sell_idx(base, k, lane)], x[col[sell_idx(base, k, lane)]], acc);
+        return fma(diag[i], x[i], acc);
     }
 };
 
@@ -57,13 +98,26 @@ struct SellF32Diff {
             const int64_t base = __ldg(sptr + s);
             const int w = (int)((__ldg(sptr + s + 1) - base) >> 5);
             const int64_t i = s * 32 + lane;
-            const int32_t *c = col + base + lane;
-            const float *v = val + base + lane;
             const float xi = i < n ? x[i] : 0.0f;
-            float acc = 0.0f;
-#pragma unroll 4
-            for (int k = 0; k < w; ++k) acc = fmaf(__ldg(v + 32 * k), x[__ldg(c + 32 * k)] - xi, acc);
-            if (i < n) epi(i, fmaf(__ldg(rsum + i), xi, acc));
+            const int2 *c2 = reinterpret_cast<const int2 *>(col + base) + lane;
+            const float2 *v2 = reinterpret_cast<const float2 *>(val + base) + lane;
+            float a0 = 0.0f, a1 = 0.0f;
+            int k = 0;
+            for (; k + 4 <= w; k += 4) {
+                const int2 ca = __ldg(c2 + 16 * k), cb = __ldg(c2 + 16 * k + 32);
+                const float2 va = __ldg(v2 + 16 * k), vb = __ldg(v2 + 16 * k + 32);
+                a0 = fmaf(va.x, x[ca.x] - xi, a0);
+                a1 = fmaf(va.y, x[ca.y] - xi, a1);
+                a0 = fmaf(vb.x, x[cb.x] - xi, a0);
+                a1 = fmaf(vb.y, x[cb.y] - xi, a1);
+            }
+            if (k < w) {
+                const int2 ca = __ldg(c2 + 16 * k);
+                const float2 va = __ldg(v2 + 16 * k);
+                a0 = fmaf(va.x, x[ca.x] - xi, a0);
+                a1 = fmaf(va.y, x[ca.y] - xi, a1);
+            }
+            if (i < n) epi(i, fmaf(__ldg(rsum + i), xi, a0 + a1));
         }
     }
 };

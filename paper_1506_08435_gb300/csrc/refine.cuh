@@ -7,24 +7,30 @@
 // x <- P(x + d) in FP64, so the bounds stay exact.  FP32 storage cuts the
 // bytes of every inner product to 8 per stored entry (from 12) and keeps the
 // work off the FP64 pipe; accuracy is recovered by the FP64 residual.
+//
+// Refinement contracts only while u32 * cond(A) stays well below 1.  When a
+// refinement step fails to halve ||gP||, the solve continues with FP64 GPCG
+// from the current iterate (same tolerance), so the result always meets the
+// FP64 KKT test; MixedStats::fallback records that this happened.
 #pragma once
 #include "gpcg.cuh"
 
 namespace nnqp {
 
 struct MixedStats {
-    int64_t spmv64 = 0, spmv32 = 0, cg = 0, phases = 0, refinements = 0, vec64 = 0, vec32 = 0;
+    int64_t spmv64 = 0, spmv32 = 0, cg = 0, phases = 0, refinements = 0, vec64 = 0, vec32 = 0, fallback = 0;
     double gp2 = 0.0;
 };
 
 template <class Team, class Op64, class Op32>
 __device__ int mixed_solve(Team &T, const Rows &R, const Op64 &A, const Op32 &A32, double lo, double hi,
                            const double *b, double *x, GpcgVecs<float> &v, float *r32, float *l32, float *h32,
-                           double tol, double inner_rtol, int max_ref, int64_t max_spmv, const GpcgCtl &ctl32,
-                           MixedStats &st) {
+                           GpcgVecs<double> &v64, double tol, double inner_rtol, int max_ref, int64_t max_spmv,
+                           const GpcgCtl &ctl32, const GpcgCtl &ctl64, MixedStats &st) {
     R.each([&](int64_t i) { x[i] = clampv(x[i], lo, hi); });
     st.vec64 += 2;
     if (!T.sync()) return ST_TIMEOUT;
+    double prev_gp2 = -1.0;
     for (int ref = 0;; ++ref) {
         double a[1] = {0.0};
         A.apply(R, x, [&](int64_t i, double ax) {
@@ -44,7 +50,31 @@ __device__ int mixed_solve(Team &T, const Rows &R, const Op64 &A, const Op32 &A3
         st.gp2 = a[0];
         if (!isfinite(st.gp2)) return ST_NUMERIC;
         if (st.gp2 <= tol * tol) return ST_OK;
-        if (ref >= max_ref || st.spmv64 + st.spmv32 >= max_spmv) return ST_NOT_CONVERGED;
+        if (st.spmv64 + st.spmv32 >= max_spmv) return ST_NOT_CONVERGED;
+        if (ref >= max_ref || (prev_gp2 > 0.0 && st.gp2 > 0.25 * prev_gp2)) {
+            // refinement stopped contracting: finish in FP64 from x
+            st.fallback = 1;
+            GpcgCtl c = ctl64;
+            c.tol = tol;
+            c.face_tol = 0.5 * tol;
+            c.max_spmv = max_spmv - st.spmv64 - st.spmv32;
+            GpcgStats gs;
+            v64.x = x;
+            const int s = gpcg_solve(T, R, A, Bounds<double>{lo, hi, nullptr, nullptr}, v64, c, gs);
+            st.spmv64 += gs.spmv;
+            st.cg += gs.cg;
+            st.phases += gs.phases;
+            st.vec64 += gs.vec;
+            st.gp2 = gs.gp2;
+            if (s == ST_TIMEOUT) return s;
+            if (v64.x != x) {
+                R.each([&](int64_t i) { x[i] = v64.x[i]; });
+                st.vec64 += 2;
+                if (!T.sync()) return ST_TIMEOUT;
+            }
+            return s;
+        }
+        prev_gp2 = st.gp2;
         ++st.refinements;
         GpcgCtl c = ctl32;
         c.tol = inner_rtol * sqrt(st.gp2);
@@ -57,6 +87,7 @@ __device__ int mixed_solve(Team &T, const Rows &R, const Op64 &A, const Op32 &A3
         st.spmv32 += is.spmv;
         st.cg += is.cg;
         st.phases += is.phases;
+        st.vec32 += is.vec;
         if (s == ST_TIMEOUT || s == ST_NUMERIC) return s;
         R.each([&](int64_t i) { x[i] = clampv(x[i] + (double)v.x[i], lo, hi); });
         st.vec64 += 2;

@@ -95,7 +95,9 @@ __device__ bool step_outputs(Team &T, const Rows &R, const GridArgs &a, const do
     return true;
 }
 
-template <int FMT>
+// One instantiation per (format, mode) so that each kernel carries only the
+// code of its own path (register allocation is per kernel).
+template <int FMT, int MODE>
 __global__ void __launch_bounds__(kSolveThreads) k_solve_grid(GridArgs a) {
     __shared__ RedSmem sm;
     GridTeam T{a.bar, a.partials, (int)gridDim.x + a.bar_extra, a.timeout_ns, 0, 0, &sm};
@@ -103,23 +105,25 @@ __global__ void __launch_bounds__(kSolveThreads) k_solve_grid(GridArgs a) {
     double *x = a.v64[0];
     R.each([&](int64_t i) { x[i] = a.c_in[a.free_node[i]]; });
     if (!T.sync()) return;
-    const int nsteps = a.mode == MODE_TRANSIENT ? a.nsteps : 1;
+    const int nsteps = MODE == MODE_TRANSIENT ? a.nsteps : 1;
     for (int step = 0; step < nsteps; ++step) {
         int status = ST_OK;
         int64_t cnt[kCounters] = {0};
         double den = a.b0norm, gp2 = 0.0;
         double *b = const_cast<double *>(a.b0);
-        if (a.mode == MODE_TRANSIENT) {
+        if (MODE == MODE_TRANSIENT) {
             if (!transient_rhs(T, R, a, x, b, den)) return;
             cnt[1] += 1;   // products with M (FP64)
         }
         if (!(den > 0.0)) den = a.den_fallback;
-        if (a.mode == MODE_MIXED) {
+        if (MODE == MODE_MIXED) {
             GpcgVecs<float> v{a.v32[0], a.v32[1], a.v32[2], a.v32[3], a.v32[4], a.v32[5],
                               a.v32[6], a.v32[7], a.v32[8], a.v32[9], a.dinv32};
+            GpcgVecs<double> v64{x, a.v64[1], a.v64[2], a.v64[3], a.v64[4], a.v64[5],
+                                 a.v64[6], a.v64[7], a.v64[8], b, a.dinv64};
             MixedStats ms;
-            status = mixed_solve(T, R, a.A, a.A32, a.lo, a.hi, b, x, v, a.v32[9], a.v32[10], a.v32[11],
-                                 a.rtol * den, a.inner_rtol, a.max_ref, a.ctl.max_spmv, a.ctl, ms);
+            status = mixed_solve(T, R, a.A, a.A32, a.lo, a.hi, b, x, v, a.v32[9], a.v32[10], a.v32[11], v64,
+                                 a.rtol * den, a.inner_rtol, a.max_ref, a.ctl.max_spmv, a.ctl, a.ctl, ms);
             if (status == ST_TIMEOUT) return;
             cnt[1] += ms.spmv64;
             cnt[2] += ms.spmv32;
@@ -128,6 +132,7 @@ __global__ void __launch_bounds__(kSolveThreads) k_solve_grid(GridArgs a) {
             cnt[5] = ms.refinements;
             cnt[6] = ms.vec64;
             cnt[7] = ms.vec32;
+            cnt[11] = ms.fallback;
             gp2 = ms.gp2;
         } else {
             GpcgVecs<double> v{x, a.v64[1], a.v64[2], a.v64[3], a.v64[4], a.v64[5],
@@ -211,15 +216,7 @@ __global__ void __launch_bounds__(256) k_kkt(SellF64 A, SellF64 M, int transient
     double s[6] = {0, 0, 0, 0, 0, 0};
     A.apply(R, x, [&](int64_t i, double ax) {
         double bi = b0[i];
-        if (transient) {
-            // (M x_prev)_i computed row-wise (the product is cheap next to the check)
-            const int64_t sl = i >> 5, lane = i & 31;
-            const int64_t base = M.sptr[sl];
-            const int w = (int)((M.sptr[sl + 1] - base) >> 5);
-            double m = M.diag[i] * xprev[i];
-            for (int k = 0; k < w; ++k) m += M.val[base + 32 * k + lane] * xprev[M.col[base + 32 * k + lane]];
-            bi += m * inv_dt;
-        }
+        if (transient) bi += M.row_product(i, xprev) * inv_dt;   // (M x_prev)_i, row-wise
         const double xi = x[i];
         const double g = ax - bi;
         const double gp = proj_grad(xi, g, lo, hi);
@@ -345,6 +342,7 @@ void fill_info(const nn_system *s, const int64_t *cnt, const double *sc, int pre
     info->refinements = cnt[5];
     info->active_lo = cnt[8];
     info->active_hi = cnt[9];
+    info->fp64_fallback = cnt[11];
     info->kkt_rel = std::sqrt(sc[0]) / sc[1];
     info->kkt_inf = NAN;
     info->objective = NAN;
@@ -408,7 +406,9 @@ nn_status run_grid(nn_system *s, const nn_solve_opts *o, int mode, int nsteps, c
     a.ctl.eta2 = 1e-3;
     a.ctl.mu = 1e-4;
     a.ctl.cg_variant = n < (1 << 20) ? 1 : 0;
+    a.ctl.cg_bound_stop = 0;
     if (const char *e = getenv("NNQP_CG_VARIANT")) a.ctl.cg_variant = atoi(e);
+    if (const char *e = getenv("NNQP_CG_BOUND_STOP")) a.ctl.cg_bound_stop = atoi(e);
     if (const char *e = getenv("NNQP_GP_MAX")) a.ctl.gp_max = atoi(e);
     if (const char *e = getenv("NNQP_ETA1")) a.ctl.eta1 = atof(e);
     if (const char *e = getenv("NNQP_ETA2")) a.ctl.eta2 = atof(e);
@@ -430,7 +430,11 @@ nn_status run_grid(nn_system *s, const nn_solve_opts *o, int mode, int nsteps, c
         NN_TRY(S.a.alloc(&a.S, (size_t)(a.m + 1) * n, st));
         NN_TRY(S.a.alloc(&a.Y, (size_t)(a.m + 1) * n, st));
     }
-    void (*kern)(GridArgs) = lbfgs ? k_lbfgs_grid : (fmt == NN_FMT_CSR ? k_solve_grid<1> : k_solve_grid<0>);
+    void (*kern)(GridArgs) = lbfgs                   ? k_lbfgs_grid
+                             : fmt == NN_FMT_CSR     ? k_solve_grid<1, MODE_STEADY>
+                             : mode == MODE_MIXED    ? k_solve_grid<0, MODE_MIXED>
+                             : mode == MODE_TRANSIENT ? k_solve_grid<0, MODE_TRANSIENT>
+                                                     : k_solve_grid<0, MODE_STEADY>;
     const int maxg = max_coresident(kern);
     int warps = kSolveThreads / 32;
     int want = (int)std::min<int64_t>((s->A64.nslices + warps - 1) / warps, (int64_t)maxg);
@@ -589,7 +593,9 @@ int mode_for(const nn_system *s, const nn_solve_opts *o) {
 }
 
 // Co-resident blocks of the steady/mixed solve kernel on the current device.
-int solve_grid_capacity() { return max_coresident(k_solve_grid<0>); }
+int solve_grid_capacity() {
+    return std::min(max_coresident(k_solve_grid<0, MODE_STEADY>), max_coresident(k_solve_grid<0, MODE_MIXED>));
+}
 
 // One steady solve with a fixed persistent grid (serving).
 nn_status serve_solve(nn_system *s, const nn_solve_opts *o, const double *c_in_dev, double *c_out_dev,

@@ -19,11 +19,20 @@ constexpr int kMaxRed = 24;       // doubles per reduction call (at most)
 constexpr int kMaxWarps = 32;
 
 struct GridBarrier {
-    unsigned int arrive;
-    unsigned int gen;
+    unsigned long long count;     // arrivals since launch (never reset)
     int error;                    // 0 = fine, else an nn_status code
     int where;                    // diagnostic: id of the wait that gave up
 };
+
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void red_release_add_u64(unsigned long long *p, unsigned long long v) {
+    asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
 
 __device__ __forceinline__ unsigned long long global_ns() {
     unsigned long long t;
@@ -63,14 +72,12 @@ __device__ __forceinline__ void block_sum(double (&v)[K], RedSmem &sm) {
 #pragma unroll
         for (int k = 0; k < K; ++k) sm.warp[warp][k] = v[k];
     __syncthreads();
-    if (warp == 0) {
+    // warp w sums the entries k = w, w + nw, ... (each in one fixed order)
+    for (int k = warp; k < K; k += nw) {
+        double t = lane < nw ? sm.warp[lane][k] : 0.0;
 #pragma unroll
-        for (int k = 0; k < K; ++k) {
-            double t = lane < nw ? sm.warp[lane][k] : 0.0;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-            if (lane == 0) sm.bcast[k] = t;
-        }
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (lane == 0) sm.bcast[k] = t;
     }
     __syncthreads();
 #pragma unroll
@@ -101,40 +108,39 @@ struct GridTeam {
     int wait_id;
     RedSmem *sm;
 
-    // Grid-wide barrier.  Thread 0 of each block arrives on a counter; the
-    // last arriver resets it and bumps the generation; the others wait for
-    // the generation to change, for at most timeout_ns, and leave with the
-    // error flag set if it does not (or if another block already set it).
+    // Grid-wide barrier.  Every block knows how many barriers it has passed
+    // (wait_id), so the k-th barrier is complete once the arrival counter
+    // reaches k * nblocks.  Thread 0 of each block arrives with a release-add
+    // (its block's writes become visible first) and polls the counter with
+    // acquire loads, for at most timeout_ns; a wait that runs out sets the
+    // error word, and a block that sees the error word set leaves as well.
     __device__ bool sync() {
         __syncthreads();
         ++wait_id;
         if (threadIdx.x == 0) {
             int ok = 1;
-            unsigned g = ld_acquire_u32(&bar->gen);
-            __threadfence();
-            unsigned prev = atomicAdd(&bar->arrive, 1u);
-            if (prev == (unsigned)nblocks - 1u) {
-                atomicExch(&bar->arrive, 0u);
-                __threadfence();
-                atomicAdd(&bar->gen, 1u);
-            } else {
-                unsigned long long t0 = global_ns();
-                unsigned spins = 0;
-                while (ld_acquire_u32(&bar->gen) == g) {
+            const unsigned long long target = (unsigned long long)wait_id * (unsigned long long)nblocks;
+            red_release_add_u64(&bar->count, 1ULL);
+            unsigned spins = 0;
+            unsigned long long t0 = 0;
+            while (ld_acquire_u64(&bar->count) < target) {
+                ++spins;
+                if ((spins & 63u) == 0) {
                     if (ld_relaxed_i32(&bar->error)) {
                         ok = 0;
                         break;
                     }
-                    if ((++spins & 31u) == 0 && global_ns() - t0 > timeout_ns) {
+                    const unsigned long long now = global_ns();
+                    if (t0 == 0) {
+                        t0 = now;
+                    } else if (now - t0 > timeout_ns) {
                         if (atomicCAS(&bar->error, 0, 7 /* NN_ERR_TIMEOUT */) == 0) bar->where = wait_id;
                         ok = 0;
                         break;
                     }
-                    __nanosleep(40);
                 }
+                if (spins > 256) __nanosleep(32);
             }
-            __threadfence();
-            if (ld_relaxed_i32(&bar->error)) ok = 0;
             sm->flag = ok;
         }
         __syncthreads();
@@ -150,16 +156,15 @@ struct GridTeam {
 #pragma unroll
             for (int k = 0; k < K; ++k) P[(size_t)k * nblocks + blockIdx.x] = v[k];
         if (!sync()) return false;
-        const int lane = threadIdx.x & 31;
-        if (threadIdx.x < 32) {
+        // warp w sums the per-block partials of entries k = w, w + nw, ...;
+        // the loads of different entries are in flight together
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+        for (int k = warp; k < K; k += nw) {
+            double t = 0.0;
+            for (int b = lane; b < nblocks; b += 32) t += __ldcg(P + (size_t)k * nblocks + b);
 #pragma unroll
-            for (int k = 0; k < K; ++k) {
-                double t = 0.0;
-                for (int b = lane; b < nblocks; b += 32) t += __ldcg(P + (size_t)k * nblocks + b);
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-                if (lane == 0) sm->bcast[k] = t;
-            }
+            for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+            if (lane == 0) sm->bcast[k] = t;
         }
         __syncthreads();
 #pragma unroll

@@ -142,7 +142,8 @@ def test_qp_steady_2d_config():
     assert np.array_equal(c[spec.dmask == 1], spec.dval[spec.dmask == 1])
     assert info["active_lo"] == int((c[red.free] == 0.0).sum()) > 0
     k2 = P.nn_kkt_residual(s, torch.tensor(c, device=DEV))
-    assert k2["kkt_rel"] == pytest.approx(k["kkt_rel"], rel=1e-6, abs=1e-15) and k2["bounds_ok"]
+    # two FP64 evaluations of a residual near 1e-11 differ in the cancellation of Ax - b
+    assert k2["kkt_rel"] == pytest.approx(k["kkt_rel"], rel=1e-3, abs=1e-15) and k2["bounds_ok"]
     assert info["kkt_rel"] <= 1e-10
 
 

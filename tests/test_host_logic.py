@@ -1,0 +1,125 @@
+"""Host-side logic that needs no GPU: the compact L-BFGS algebra used by the
+device solver, the seeded input generator, and the multi-process replica
+path of the benchmark (gloo, world size 2)."""
+import ctypes
+import os
+import subprocess
+import sys
+
+import numpy as np
+import pytest
+
+import nn_inputs as I
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+CSRC = os.path.join(ROOT, "paper_1506_08435_gb300", "csrc")
+
+
+@pytest.fixture(scope="module")
+def lbfgs_lib(tmp_path_factory):
+    d = tmp_path_factory.mktemp("lb")
+    src = d / "lb.cpp"
+    src.write_text('#include "lbfgs_small.h"\n'
+                   'extern "C" int coef(int k, const double* SY, const double* YY, const double* u,'
+                   ' const double* v, double gamma, double* cs, double* cy) {'
+                   ' return nnqp::lbfgs_coefficients(k, SY, YY, u, v, gamma, cs, cy) ? 1 : 0; }\n')
+    so = d / "lb.so"
+    subprocess.check_call(["g++", "-O2", "-shared", "-fPIC", "-I", CSRC, str(src), "-o", str(so)])
+    L = ctypes.CDLL(str(so))
+    dp = ctypes.POINTER(ctypes.c_double)
+    L.coef.argtypes = [ctypes.c_int, dp, dp, dp, dp, ctypes.c_double, dp, dp]
+    return L
+
+
+def two_loop(S, Y, g, gamma):
+    """Textbook L-BFGS two-loop recursion H g (pairs oldest first)."""
+    q = g.copy()
+    k = S.shape[1]
+    alpha = np.zeros(k)
+    for i in range(k - 1, -1, -1):
+        rho = 1.0 / (S[:, i] @ Y[:, i])
+        alpha[i] = rho * (S[:, i] @ q)
+        q -= alpha[i] * Y[:, i]
+    r = gamma * q
+    for i in range(k):
+        rho = 1.0 / (S[:, i] @ Y[:, i])
+        beta = rho * (Y[:, i] @ r)
+        r += S[:, i] * (alpha[i] - beta)
+    return r
+
+
+@pytest.mark.parametrize("k", [1, 2, 4, 6])
+def test_compact_lbfgs_equals_two_loop(lbfgs_lib, k):
+    rng = np.random.default_rng(k)
+    n = 30
+    B = rng.normal(size=(n, n))
+    A = B @ B.T + n * np.eye(n)          # SPD: y = A s gives s'y > 0
+    S = rng.normal(size=(n, k))
+    Y = A @ S
+    g = rng.normal(size=n)
+    gamma = (S[:, -1] @ Y[:, -1]) / (Y[:, -1] @ Y[:, -1])
+    SY = np.zeros((16, 16))
+    YY = np.zeros((16, 16))
+    SY[:k, :k] = S.T @ Y
+    YY[:k, :k] = Y.T @ Y
+    u, v = S.T @ g, Y.T @ g
+    cs, cy = np.zeros(16), np.zeros(16)
+    p = lambda a: np.ascontiguousarray(a, np.float64).ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    SYc, YYc, uc, vc = [np.ascontiguousarray(a, np.float64) for a in (SY, YY, u, v)]
+    assert lbfgs_lib.coef(k, p(SYc), p(YYc), p(uc), p(vc), gamma, cs.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                          cy.ctypes.data_as(ctypes.POINTER(ctypes.c_double))) == 1
+    hg = gamma * g + S @ cs[:k] + Y @ cy[:k]
+    ref = two_loop(S, Y, g, gamma)
+    assert np.allclose(hg, ref, rtol=1e-10, atol=1e-12 * np.abs(ref).max())
+
+
+def test_splitmix64_published_vector():
+    """SplitMix64 from state 0 (Steele, Lea & Flood 2014): the first outputs
+    are 0xe220a8397b1dcdaf, 0x6e789e6aa1b965f4, 0x06c45d188009454f."""
+    r = I.SplitMix64(0, 0)
+    assert [r.u64() for _ in range(3)] == [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
+
+
+def test_inputs_are_deterministic_and_shaped_like_the_workloads():
+    a, b = I.config4_instance(17), I.config4_instance(17)
+    assert a.nx == b.nx and np.array_equal(a.coef, b.coef) and np.array_equal(a.f_elem, b.f_elem)
+    sizes = [I.config4_instance(i).nx for i in range(200)]
+    assert min(sizes) >= 20 and max(sizes) <= 200 and len(set(sizes)) > 50
+    s = I.config2_transient_3d(n=6)
+    assert s.coef.shape == (6 * 6 ** 3, 3) and np.all(np.linalg.norm(s.coef, axis=1) >= 0.1 - 1e-15)
+    t = I.serve_arrivals(200.0, 10.0)
+    assert 1800 < len(t) < 2200 and all(np.diff(t) > 0)
+
+
+WORKER = r'''
+import os, sys, json
+sys.path.insert(0, sys.argv[1])
+import torch.distributed as dist
+import bench
+d, rank, ws = bench.dist_init()
+assert ws == 2
+bench.barrier(d)
+m = bench.max_over_ranks(d, 10.0 + rank)
+# shard independent units across ranks (no data-path collective)
+import nn_inputs as I
+mine = [I.config4_instance(i, nmin=8, nmax=10).nx for i in range(rank, 6, ws)]
+print(json.dumps({"rank": rank, "max": m, "units": len(mine)}))
+d.destroy_process_group()
+'''
+
+
+def test_replica_timing_path_world_size_2(tmp_path):
+    w = tmp_path / "w.py"
+    w.write_text(WORKER)
+    procs = []
+    for rank in range(2):
+        env = dict(os.environ, RANK=str(rank), LOCAL_RANK=str(rank), WORLD_SIZE="2",
+                   MASTER_ADDR="127.0.0.1", MASTER_PORT="29531", CUDA_VISIBLE_DEVICES="")
+        procs.append(subprocess.Popen([sys.executable, str(w), ROOT], env=env, stdout=subprocess.PIPE,
+                                      stderr=subprocess.PIPE, text=True))
+    outs = [p.communicate(timeout=120) for p in procs]
+    import json
+    res = [json.loads(o[0].strip().splitlines()[-1]) for o in outs]
+    assert all(p.returncode == 0 for p in procs), [o[1][-500:] for o in outs]
+    assert all(r["max"] == 11.0 for r in res)
+    assert sum(r["units"] for r in res) == 6

@@ -477,13 +477,17 @@ def main():
     kern_ms = float(np.mean(r["kern_ms"]))
     kern_bytes = float(np.mean(r["kern_bytes"]))
     achieved = kern_bytes / (kern_ms / 1e3) / 1e9
-    tfile = os.path.join(ROOT, "profiles", "traffic_%s.json" % r["config"]["workload"])
+    # DRAM bytes per launch of the solve kernel from the committed ncu summary
+    # of this workload (a line "dram_bytes_per_launch: N"), if there is one
+    tfile = os.path.join(ROOT, "profiles", "k_solve_grid_%s.md" % r["config"]["workload"])
     traffic = None
     if os.path.exists(tfile):
-        try:
-            traffic = json.load(open(tfile)).get("dram_bytes_per_launch")
-        except Exception:
-            traffic = None
+        for line in open(tfile):
+            if line.strip().startswith("dram_bytes_per_launch:"):
+                try:
+                    traffic = float(line.split(":", 1)[1].split()[0])
+                except ValueError:
+                    traffic = None
     infos = r["infos"]
     line = {"metric": r["metric"], "value": value, "unit": r["unit"], "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,

@@ -72,7 +72,8 @@ __global__ void __launch_bounds__(TPB) k_batch(const BatchInst *__restrict__ ins
                                  w6 + 7 * n, w6 + 8 * n, I.b0, I.dinv64};
             MixedStats ms;
             status = mixed_solve(T, R, A, A32, I.lo, I.hi, I.b0, x, v, w + 9 * n, w + 10 * n, w + 11 * n, v64,
-                                 rtol * I.den, inner_rtol, max_ref, ctl.max_spmv, ctl, ctl, ms);
+                                 rtol * I.den, inner_rtol, max_ref, ctl.max_spmv, inner_product_cap(n), ctl, ctl,
+                                 ms);
             cnt[1] = ms.spmv64;
             cnt[2] = ms.spmv32;
             cnt[3] = ms.cg;

@@ -17,6 +17,14 @@
 
 namespace nnqp {
 
+// Products allowed to one FP32 inner solve: CG needs O(sqrt(cond)) steps
+// and cond grows like n^(2/d); 8 sqrt(n) (at least 4000) is ample where FP32
+// converges at all.
+__host__ __device__ __forceinline__ int64_t inner_product_cap(int64_t n) {
+    const int64_t c = (int64_t)(8.0 * sqrt((double)n));
+    return c > 4000 ? c : 4000;
+}
+
 struct MixedStats {
     int64_t spmv64 = 0, spmv32 = 0, cg = 0, phases = 0, refinements = 0, vec64 = 0, vec32 = 0, fallback = 0;
     double gp2 = 0.0;
@@ -26,7 +34,7 @@ template <class Team, class Op64, class Op32>
 __device__ int mixed_solve(Team &T, const Rows &R, const Op64 &A, const Op32 &A32, double lo, double hi,
                            const double *b, double *x, GpcgVecs<float> &v, float *r32, float *l32, float *h32,
                            GpcgVecs<double> &v64, double tol, double inner_rtol, int max_ref, int64_t max_spmv,
-                           const GpcgCtl &ctl32, const GpcgCtl &ctl64, MixedStats &st) {
+                           int64_t inner_cap, const GpcgCtl &ctl32, const GpcgCtl &ctl64, MixedStats &st) {
     R.each([&](int64_t i) { x[i] = clampv(x[i], lo, hi); });
     st.vec64 += 2;
     if (!T.sync()) return ST_TIMEOUT;
@@ -80,7 +88,10 @@ __device__ int mixed_solve(Team &T, const Rows &R, const Op64 &A, const Op32 &A3
         c.tol = inner_rtol * sqrt(st.gp2);
         if (c.tol < 0.25 * tol) c.tol = 0.25 * tol;
         c.face_tol = 0.5 * c.tol;
+        // an inner solve that cannot reach its tolerance in FP32 (u32 * cond(A)
+        // near 1) is cut off; the contraction test above then decides
         c.max_spmv = max_spmv - st.spmv64 - st.spmv32;
+        if (c.max_spmv > inner_cap) c.max_spmv = inner_cap;
         GpcgStats is;
         Bounds<float> B{0.0, 0.0, l32, h32};
         int s = gpcg_solve(T, R, A32, B, v, c, is);

@@ -123,7 +123,8 @@ __global__ void __launch_bounds__(kSolveThreads) k_solve_grid(GridArgs a) {
                                  a.v64[6], a.v64[7], a.v64[8], b, a.dinv64};
             MixedStats ms;
             status = mixed_solve(T, R, a.A, a.A32, a.lo, a.hi, b, x, v, a.v32[9], a.v32[10], a.v32[11], v64,
-                                 a.rtol * den, a.inner_rtol, a.max_ref, a.ctl.max_spmv, a.ctl, a.ctl, ms);
+                                 a.rtol * den, a.inner_rtol, a.max_ref, a.ctl.max_spmv,
+                                 inner_product_cap(a.n), a.ctl, a.ctl, ms);
             if (status == ST_TIMEOUT) return;
             cnt[1] += ms.spmv64;
             cnt[2] += ms.spmv32;
@@ -436,8 +437,14 @@ nn_status run_grid(nn_system *s, const nn_solve_opts *o, int mode, int nsteps, c
                              : mode == MODE_TRANSIENT ? k_solve_grid<0, MODE_TRANSIENT>
                                                      : k_solve_grid<0, MODE_STEADY>;
     const int maxg = max_coresident(kern);
-    int warps = kSolveThreads / 32;
-    int want = (int)std::min<int64_t>((s->A64.nslices + warps - 1) / warps, (int64_t)maxg);
+    // one slice per warp at least; grids of up to one block per SM while that
+    // covers the rows in a few slices per warp (fewer barrier arrivals), the
+    // full co-resident grid for large systems (more loads in flight)
+    const int warps = kSolveThreads / 32;
+    const int64_t by_rows = (s->A64.nslices + warps - 1) / warps;
+    const int sms = device_sms();
+    int want = (int)std::min<int64_t>(by_rows, by_rows <= 4 * sms ? (int64_t)sms : (int64_t)maxg);
+    want = std::min(want, maxg);
     if (o->grid_blocks > 0) want = std::min(o->grid_blocks, maxg);
     want = std::max(want, 1);
     // NNQP_TEST_STALL_BARRIER=1 makes the grid barrier wait for one block

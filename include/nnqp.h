@@ -236,6 +236,33 @@ nn_status nn_kkt_residual(const nn_system *s, const double *c, const double *c_p
  * operator (x, y still FP64).  Stream-ordered, asynchronous. */
 nn_status nn_spmv(const nn_system *s, const double *x, double *y, int format, int precision, void *stream);
 
+/* y = A x with the FP32-value operator (the product of nn_spmv with
+ * NN_FMT_SELL and NN_PREC_MIXED) WITHOUT allocating any device memory.
+ * The paper has no counterpart; this entry point exists for callers that
+ * must not allocate once they are running: for example a real-time loop
+ * where cudaMalloc/cudaFree may synchronize the whole device and take an
+ * unbounded time, or an application whose device memory is owned entirely
+ * by another allocator and has no headroom.  nn_spmv(NN_PREC_MIXED)
+ * allocates a temporary FP32 copy of x per call; this variant keeps that
+ * copy in one fixed array inside the library instead.
+ *   - x, y: device arrays of n_free doubles (as for nn_spmv); the system
+ *     must have been assembled with build_mixed = 1.
+ *   - Limit: n_free <= 4,194,304 (the array is 16 MiB of FP32).  Larger
+ *     systems are rejected with NN_ERR_INVALID_ARG and a message.
+ *   - Every GPU on which this library is loaded holds that 16 MiB array
+ *     until the process exits.
+ *   - The first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture begins.
+ *   - All calls share the one array and it keeps the last call's contents
+ *     (each call overwrites what it reads, nothing has to start at zero).
+ *     Calls whose kernels overlap on the GPU -- on different streams, or
+ *     from different host threads -- race on it: order them on one stream
+ *     or serialize them.
+ *   - Launches two kernels on `stream`; no cudaMalloc, cudaFree or other
+ *     allocating call.  Asynchronous. */
+nn_status nn_spmv_mixed_noalloc(const nn_system *s, const double *x, double *y, void *stream);
+
 /* --------------------------------------------------------------- batching */
 
 /* Solves `count` independent steady systems in ONE persistent launch: one

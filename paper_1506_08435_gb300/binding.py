@@ -100,6 +100,7 @@ class nn_serve_stats_t(ctypes.Structure):
 EXPORTS = ["nn_last_error", "nn_version", "nn_kernel_launches", "nn_mesh_counts", "nn_mesh_structured", "nn_assemble_opts_default",
            "nn_assemble", "nn_system_destroy", "nn_system_describe", "nn_system_copy_out",
            "nn_solve_opts_default", "nn_qp_solve", "nn_step", "nn_transient", "nn_kkt_residual", "nn_spmv",
+           "nn_spmv_mixed_noalloc",
            "nn_batch_solve", "nn_batch_autotune", "nn_serve_opts_default", "nn_serve_create",
            "nn_serve_submit", "nn_serve_poll", "nn_serve_drain", "nn_serve_stats", "nn_serve_destroy"]
 
@@ -137,6 +138,7 @@ def lib():
     L.nn_transient.argtypes = [vp, vp, c_int, vp, vp, c_int, POINTER(nn_solve_opts), vp, POINTER(nn_solve_info)]
     L.nn_kkt_residual.argtypes = [vp, vp, vp, c_int, POINTER(c_double), vp]
     L.nn_spmv.argtypes = [vp, vp, vp, c_int, c_int, vp]
+    L.nn_spmv_mixed_noalloc.argtypes = [vp, vp, vp, vp]
     L.nn_batch_solve.argtypes = [c_int, POINTER(vp), POINTER(vp), POINTER(nn_solve_opts), vp,
                                  POINTER(nn_solve_info)]
     L.nn_batch_autotune.argtypes = [c_int, POINTER(vp), POINTER(nn_solve_opts), vp, POINTER(c_int)]
@@ -354,6 +356,13 @@ def nn_kkt_residual(sys, c, c_prev=None, stream=None):
 
 def nn_spmv(sys, x, y, format=NN_FMT_SELL, precision=NN_PREC_FP64, stream=None):
     _check(lib().nn_spmv(sys.handle, _ptr(x)[0], _ptr(y)[0], format, precision, _stream(stream)))
+    return y
+
+
+def nn_spmv_mixed_noalloc(sys, x, y, stream=None):
+    """y = A x (FP32-value operator) using the library's fixed scratch array
+    instead of a per-call allocation (see include/nnqp.h)."""
+    _check(lib().nn_spmv_mixed_noalloc(sys.handle, _ptr(x)[0], _ptr(y)[0], _stream(stream)))
     return y
 
 

@@ -31,6 +31,7 @@ int mode_for(const nn_system *s, const nn_solve_opts *o);
 nn_status kkt_impl(const nn_system *s, const double *c, const double *c_prev, int memory, double out[4],
                    cudaStream_t st);
 nn_status spmv_impl(const nn_system *s, const double *x, double *y, int format, int precision, cudaStream_t st);
+nn_status spmv_mixed_noalloc_impl(const nn_system *s, const double *x, double *y, cudaStream_t st);
 nn_status check_opts(const nn_solve_opts *o);
 
 nn_status check_opts(const nn_solve_opts *o) {
@@ -259,6 +260,15 @@ nn_status nn_spmv(const nn_system *s, const double *x, double *y, int format, in
         return NN_ERR_INVALID_ARG;
     }
     return spmv_impl(s, x, y, format, precision, S(stream));
+}
+
+nn_status nn_spmv_mixed_noalloc(const nn_system *s, const double *x, double *y, void *stream) {
+    clear_error();
+    if (!s || !x || !y) {
+        set_error("nn_spmv_mixed_noalloc: NULL argument");
+        return NN_ERR_INVALID_ARG;
+    }
+    return spmv_mixed_noalloc_impl(s, x, y, S(stream));
 }
 
 }  // extern "C"

@@ -6,6 +6,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <algorithm>
+#include <mutex>
 #include "internal.h"
 #include "gpcg.cuh"
 #include "refine.cuh"
@@ -568,6 +569,67 @@ nn_status spmv_impl(const nn_system *s, const double *x, double *y, int format, 
     }
     if (format == NN_FMT_CSR) (k_spmvcsr<<<nb, 256, 0, st>>>(viewcsr(s), x, y), ::nnqp::count_launch());
     else (k_spmv64<<<nb, 256, 0, st>>>(view64(s), x, y), ::nnqp::count_launch());
+    NN_CUDA_TRY(cudaGetLastError());
+    return NN_OK;
+}
+
+// ------------------------------------------------------------------ no-allocation product
+//
+// nn_spmv_mixed_noalloc computes the same FP32-value product as nn_spmv with
+// NN_PREC_MIXED, but keeps the FP32 copy of x in the file-scope array below
+// instead of allocating it per call.  Maximum: kNoAllocMaxFree unknowns
+// (16 MiB of FP32).  The array exists on every device that loads this
+// library, for the life of the process; all calls share it, so calls that
+// overlap on the GPU race on it.  Nothing in it has to start at zero: every
+// call overwrites the first NF entries before reading them.
+
+constexpr int64_t kNoAllocMaxFree = 1LL << 22;
+static __device__ __align__(256) float g_noalloc_x32[kNoAllocMaxFree];
+
+namespace {
+std::mutex g_noalloc_mu;
+constexpr int kNoAllocMaxDevices = 64;
+float *g_noalloc_ptr[kNoAllocMaxDevices] = {nullptr};
+}  // namespace
+
+// Device address of the scratch array on the current device, looked up once
+// per device with that device current (host code may not use the symbol itself).
+static nn_status noalloc_scratch(float **out) {
+    int dev = 0;
+    NN_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kNoAllocMaxDevices) {
+        set_error("nn_spmv_mixed_noalloc: device %d is beyond the supported %d devices", dev, kNoAllocMaxDevices);
+        return NN_ERR_INVALID_ARG;
+    }
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_x32);
+        if (e != cudaSuccess || !p) {
+            set_error("nn_spmv_mixed_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
+            return NN_ERR_CUDA;
+        }
+        g_noalloc_ptr[dev] = (float *)p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return NN_OK;
+}
+
+nn_status spmv_mixed_noalloc_impl(const nn_system *s, const double *x, double *y, cudaStream_t st) {
+    if (!s->has_mixed) {
+        set_error("nn_spmv_mixed_noalloc: system has no FP32 copy (build_mixed = 0)");
+        return NN_ERR_INVALID_ARG;
+    }
+    if (s->NF > kNoAllocMaxFree) {
+        set_error("nn_spmv_mixed_noalloc: %lld unknowns exceed the static scratch limit of %lld",
+                  (long long)s->NF, (long long)kNoAllocMaxFree);
+        return NN_ERR_INVALID_ARG;
+    }
+    float *x32 = nullptr;
+    NN_TRY(noalloc_scratch(&x32));
+    const int nb = (int)std::max<int64_t>((s->A64.nslices + 7) / 8, 1);
+    (k_to_f32<<<(unsigned)((s->NF + 255) / 256), 256, 0, st>>>(s->NF, x, x32), count_launch());
+    (k_spmv32<<<nb, 256, 0, st>>>(view32(s), x32, y), count_launch());
     NN_CUDA_TRY(cudaGetLastError());
     return NN_OK;
 }

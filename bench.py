@@ -260,7 +260,8 @@ def run_transient(P, torch, args, rank):
                 nnz_free=None,
                 config={"workload": "transient3d_n40_dt0.01_50steps", "nodes": spec.n_nodes,
                         "tets": spec.n_elems, "qp_per_step": nsteps, "rtol": args.rtol,
-                        "l2": "flushed between steps (256 MB write)", "solver": args.solver, "precision": "fp64"},
+                        "l2": "flushed between steps (256 MB write)", "solver": args.solver, "precision": "fp64",
+                        "first_iterate": "projected 2c^n - c^(n-1)"},
                 dtype="f64", unit="QP solves/s", metric="QP solves/s")
 
 
@@ -348,7 +349,7 @@ def run_batch(P, torch, args, rank):
     return dict(times=times, infos=infos, kern_ms=[o[0]["time_ms"] for o in outs],
                 kern_bytes=[sum(i["bytes_algo"] for i in o) for o in outs], units_per_step=count, e2e=None,
                 h2d=0, d2h=0, clocks=clocks, launches=launches,
-                config={"workload": "batch2d_%d" % count, "instances": count, "threads_per_block": tuned,
+                config={"workload": "batch2d_%d" % count, "instances": count, "threads_per_block": tuned // 100, "ctas_per_instance": tuned % 100,
                         "precision": args.precision, "rtol": args.rtol, "l2": "flushed between steps"},
                 dtype="f64" if prec == P.NN_PREC_FP64 else "f32+f64", unit="QP solves/s", metric="QP solves/s")
 

@@ -178,6 +178,9 @@ typedef struct {
     int grid_blocks;     /* persistent grid size; 0 = chosen from the size */
     double wait_timeout_s; /* bound on every device-side wait (default 5 s) */
     double inner_rtol;   /* mixed: relative tolerance of each inner solve (default 1e-4) */
+    int extrapolate;     /* transient: 1 (default) starts the QP of step n+1 from the box
+                            projection of 2 c^(n) - c^(n-1) (the QP and its solution are
+                            unchanged, only the first iterate moves); 0 starts from c^(n) */
 } nn_solve_opts;
 
 void nn_solve_opts_default(nn_solve_opts *o);
@@ -197,6 +200,9 @@ typedef struct {
     int64_t active_lo, active_hi; /* entries exactly at lo / hi */
     int64_t fp64_fallback; /* mixed: 1 if refinement stopped contracting and the solve
                               finished with FP64 iterations (the result still meets rtol) */
+    double flops64_algo;   /* algorithmic FP64 operations: 2 nnz per FP64 product plus the
+                              arithmetic of the fused vector passes */
+    double flops_algo;     /* the same over all precisions */
 } nn_solve_info;
 
 /* Solves the steady QP  min 1/2 x'Ax - x'b0, lo <= x <= hi  over the free
@@ -265,20 +271,24 @@ nn_status nn_spmv_mixed_noalloc(const nn_system *s, const double *x, double *y, 
 
 /* --------------------------------------------------------------- batching */
 
-/* Solves `count` independent steady systems in ONE persistent launch: one
- * thread block per system, systems taken largest first from a device work
- * counter, block shape chosen by the autotuner (nn_batch_autotune) or the
- * default.  c[i] is the full node vector of system i (device memory).
- * infos: NULL or [count].  Mixed precision uses FP32 inner solves with FP64
- * refinement per system.  Synchronizes. */
+/* Solves `count` independent steady systems in ONE persistent launch.
+ * Each system is solved either by one thread block, or by one thread-block
+ * cluster of 4/8/16 CTAs on as many SMs (hardware cluster barriers,
+ * reductions through distributed shared memory); systems are taken largest
+ * first from a device work counter.  The shape is the autotuner's choice
+ * (nn_batch_autotune) or 256 threads x 1 CTA.  c[i] is the full node vector
+ * of system i (device memory).  infos: NULL or [count].  Mixed precision
+ * uses FP32 inner solves with FP64 refinement per system.  Synchronizes. */
 nn_status nn_batch_solve(int count, nn_system *const *systems, double *const *c, const nn_solve_opts *o,
                          void *stream, nn_solve_info *infos);
 
-/* Times candidate block shapes (threads per block) on a sample of the
- * batch for a few iterations and keeps the fastest for later
- * nn_batch_solve calls in this process; *best_threads receives it. */
+/* Times candidate launch shapes (threads per block x CTAs per system:
+ * 128x1, 256x1, 512x1, 256x4, 256x8, 256x16) on the batch's largest systems
+ * (up to 256) under a cap of 1500 products each, and keeps the shape with
+ * the shortest elapsed time for later nn_batch_solve calls in this process.
+ * *best_shape receives threads * 100 + CTAs (e.g. 25608). */
 nn_status nn_batch_autotune(int count, nn_system *const *systems, const nn_solve_opts *o, void *stream,
-                            int *best_threads);
+                            int *best_shape);
 
 /* ---------------------------------------------------------------- serving */
 

@@ -69,14 +69,15 @@ class nn_system_desc(ctypes.Structure):
 class nn_solve_opts(ctypes.Structure):
     _fields_ = [("solver", c_int), ("precision", c_int), ("format", c_int), ("rtol", c_double),
                 ("max_iter", c_int64), ("lbfgs_m", c_int), ("grid_blocks", c_int), ("wait_timeout_s", c_double),
-                ("inner_rtol", c_double)]
+                ("inner_rtol", c_double), ("extrapolate", c_int)]
 
 
 class nn_solve_info(ctypes.Structure):
     _fields_ = [("status", c_int), ("iterations", c_int64), ("spmv", c_int64), ("spmv64", c_int64),
                 ("cg_iters", c_int64), ("refinements", c_int64), ("kkt_rel", c_double), ("kkt_inf", c_double),
                 ("objective", c_double), ("time_ms", c_double), ("bytes_algo", c_double),
-                ("active_lo", c_int64), ("active_hi", c_int64), ("fp64_fallback", c_int64)]
+                ("active_lo", c_int64), ("active_hi", c_int64), ("fp64_fallback", c_int64),
+                ("flops64_algo", c_double), ("flops_algo", c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

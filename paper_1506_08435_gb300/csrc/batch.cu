@@ -6,6 +6,7 @@
 // instantiated for a one-block team.
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <numeric>
@@ -34,10 +35,72 @@ struct BatchInst {
     double *c;          // full node vector: warm start in, solution out
     double *w64;        // 10 n doubles
     float *w32;         // 12 n floats (mixed)
+    uint8_t *fm;        // n bytes: face mask of the CG phases
 };
 
 constexpr int kBatchCounters = 9;
 
+// Solves instance `id` with team T; this CTA owns the rows R of it.
+template <int MIXED, class Team>
+__device__ void solve_instance(Team &T, const Rows &R, const BatchInst &I, int id, unsigned rank, unsigned size,
+                               const GpcgCtl &ctl, double rtol, double inner_rtol, int max_ref, int64_t *counters,
+                               double *scalars) {
+    const int64_t n = I.n;
+    double *x = I.w64;
+    R.each([&](int64_t i) { x[i] = I.c[I.free_node[i]]; });
+    if (!T.sync()) return;
+    const SellF64 A{n, I.nslices, I.sptr, I.col, I.val, I.diag};
+    int64_t cnt[kBatchCounters] = {0};
+    double gp2 = 0.0;
+    int status;
+    if (MIXED) {
+        float *w = I.w32;
+        GpcgVecs<float> v{w, w + n, w + 2 * n, w + 3 * n, w + 4 * n, w + 5 * n, w + 6 * n, w + 7 * n, w + 8 * n,
+                          w + 9 * n, I.dinv32, I.fm};
+        const SellF32Diff A32{n, I.nslices, I.sptr, I.col, I.val32, I.rsum32};
+        double *w6 = I.w64;
+        GpcgVecs<double> v64{x, w6 + n, w6 + 2 * n, w6 + 3 * n, w6 + 4 * n, w6 + 5 * n, w6 + 6 * n,
+                             w6 + 7 * n, w6 + 8 * n, I.b0, I.dinv64, I.fm};
+        MixedStats ms;
+        status = mixed_solve<0>(T, R, A, A32, I.lo, I.hi, I.b0, x, v, w + 9 * n, w + 10 * n, w + 11 * n, v64,
+                                rtol * I.den, inner_rtol, max_ref, ctl.max_spmv, inner_product_cap(n), ctl, ctl, ms);
+        cnt[1] = ms.spmv64;
+        cnt[2] = ms.spmv32;
+        cnt[3] = ms.cg;
+        cnt[4] = ms.phases;
+        cnt[5] = ms.refinements;
+        cnt[6] = ms.vec64;
+        cnt[7] = ms.vec32;
+        cnt[8] = ms.fallback;
+        gp2 = ms.gp2;
+    } else {
+        double *w = I.w64;
+        GpcgVecs<double> v{w, w + n, w + 2 * n, w + 3 * n, w + 4 * n, w + 5 * n, w + 6 * n, w + 7 * n,
+                           w + 8 * n, I.b0, I.dinv64, I.fm};
+        GpcgCtl c = ctl;
+        c.tol = rtol * I.den;
+        c.face_tol = 0.5 * c.tol;
+        GpcgStats gs;
+        status = gpcg_solve<Team, SellF64, double, 0>(T, R, A, Bounds<double>{I.lo, I.hi, nullptr, nullptr}, v, c, gs);
+        x = v.x;
+        cnt[1] = gs.spmv;
+        cnt[3] = gs.cg;
+        cnt[4] = gs.phases;
+        cnt[6] = gs.vec;
+        gp2 = gs.gp2;
+    }
+    R.each([&](int64_t i) { I.c[I.free_node[i]] = x[i]; });
+    for (int64_t v = (int64_t)rank * blockDim.x + threadIdx.x; v < I.N; v += (int64_t)size * blockDim.x)
+        if (I.dmask[v]) I.c[v] = I.dval[v];
+    if (rank == 0 && threadIdx.x == 0) {
+        cnt[0] = status;
+        for (int k = 0; k < kBatchCounters; ++k) counters[(int64_t)id * kBatchCounters + k] = cnt[k];
+        scalars[2 * id] = gp2;
+        scalars[2 * id + 1] = I.den;
+    }
+}
+
+// One thread block per instance.
 template <int TPB, int MIXED>
 __global__ void __launch_bounds__(TPB) k_batch(const BatchInst *__restrict__ insts, const int *__restrict__ order,
                                                int count, unsigned *next, GpcgCtl ctl, double rtol,
@@ -53,63 +116,59 @@ __global__ void __launch_bounds__(TPB) k_batch(const BatchInst *__restrict__ ins
         if (q >= count) return;
         const int id = order[q];
         const BatchInst I = insts[id];
-        const int64_t n = I.n;
-        const Rows R{0, I.nslices, n};
-        double *x = I.w64;
-        R.each([&](int64_t i) { x[i] = I.c[I.free_node[i]]; });
-        __syncthreads();
-        const SellF64 A{n, I.nslices, I.sptr, I.col, I.val, I.diag};
-        int64_t cnt[kBatchCounters] = {0};
-        double gp2 = 0.0;
-        int status;
-        if (MIXED) {
-            float *w = I.w32;
-            GpcgVecs<float> v{w, w + n, w + 2 * n, w + 3 * n, w + 4 * n, w + 5 * n, w + 6 * n, w + 7 * n, w + 8 * n,
-                              w + 9 * n, I.dinv32};
-            const SellF32Diff A32{n, I.nslices, I.sptr, I.col, I.val32, I.rsum32};
-            double *w6 = I.w64;
-            GpcgVecs<double> v64{x, w6 + n, w6 + 2 * n, w6 + 3 * n, w6 + 4 * n, w6 + 5 * n, w6 + 6 * n,
-                                 w6 + 7 * n, w6 + 8 * n, I.b0, I.dinv64};
-            MixedStats ms;
-            status = mixed_solve(T, R, A, A32, I.lo, I.hi, I.b0, x, v, w + 9 * n, w + 10 * n, w + 11 * n, v64,
-                                 rtol * I.den, inner_rtol, max_ref, ctl.max_spmv, inner_product_cap(n), ctl, ctl,
-                                 ms);
-            cnt[1] = ms.spmv64;
-            cnt[2] = ms.spmv32;
-            cnt[3] = ms.cg;
-            cnt[4] = ms.phases;
-            cnt[5] = ms.refinements;
-            cnt[6] = ms.vec64;
-            cnt[7] = ms.vec32;
-            cnt[8] = ms.fallback;
-            gp2 = ms.gp2;
-        } else {
-            double *w = I.w64;
-            GpcgVecs<double> v{w, w + n, w + 2 * n, w + 3 * n, w + 4 * n, w + 5 * n, w + 6 * n, w + 7 * n,
-                               w + 8 * n, I.b0, I.dinv64};
-            GpcgCtl c = ctl;
-            c.tol = rtol * I.den;
-            c.face_tol = 0.5 * c.tol;
-            GpcgStats gs;
-            status = gpcg_solve(T, R, A, Bounds<double>{I.lo, I.hi, nullptr, nullptr}, v, c, gs);
-            x = v.x;
-            cnt[1] = gs.spmv;
-            cnt[3] = gs.cg;
-            cnt[4] = gs.phases;
-            cnt[6] = gs.vec;
-            gp2 = gs.gp2;
-        }
-        R.each([&](int64_t i) { I.c[I.free_node[i]] = x[i]; });
-        for (int64_t v = threadIdx.x; v < I.N; v += blockDim.x)
-            if (I.dmask[v]) I.c[v] = I.dval[v];
-        if (threadIdx.x == 0) {
-            cnt[0] = status;
-            for (int k = 0; k < kBatchCounters; ++k) counters[(int64_t)id * kBatchCounters + k] = cnt[k];
-            scalars[2 * id] = gp2;
-            scalars[2 * id + 1] = I.den;
-        }
+        solve_instance<MIXED>(T, Rows{0, I.nslices, I.n}, I, id, 0, 1, ctl, rtol, inner_rtol, max_ref, counters,
+                              scalars);
         __syncthreads();
     }
+}
+
+__device__ __forceinline__ unsigned cluster_rank() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ unsigned cluster_size() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+    return r;
+}
+
+// One thread-block cluster per instance: the instance's slices are split
+// over the cluster's CTAs (one per SM), barriers are the hardware cluster
+// barrier, reductions go through distributed shared memory.
+template <int TPB, int MIXED>
+__global__ void __launch_bounds__(TPB) k_batch_cluster(const BatchInst *__restrict__ insts,
+                                                       const int *__restrict__ order, int count, unsigned *next,
+                                                       GpcgCtl ctl, double rtol, double inner_rtol, int max_ref,
+                                                       int64_t *counters, double *scalars) {
+    __shared__ RedSmem sm;
+    __shared__ double xch[2 * kMaxRed];
+    __shared__ int s_q;
+    const unsigned rank = cluster_rank(), size = cluster_size();
+    ClusterTeam T{&sm, xch, rank, size, 0};
+    for (;;) {
+        if (rank == 0 && threadIdx.x == 0) s_q = (int)atomicAdd(next, 1u);
+        T.sync();
+        // every CTA reads the instance index taken by CTA 0
+        __shared__ int s_q0;
+        if (threadIdx.x == 0) {
+            const uint32_t local = (uint32_t)__cvta_generic_to_shared(&s_q);
+            uint32_t remote;
+            asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(local), "r"(0u));
+            int q;
+            asm volatile("ld.shared::cluster.s32 %0, [%1];" : "=r"(q) : "r"(remote) : "memory");
+            s_q0 = q;
+        }
+        T.sync();
+        const int q = s_q0;
+        if (q >= count) break;
+        const int id = order[q];
+        const BatchInst I = insts[id];
+        solve_instance<MIXED>(T, rows_of_block(I.n, I.nslices, (int)rank, (int)size), I, id, rank, size, ctl, rtol,
+                              inner_rtol, max_ref, counters, scalars);
+        T.sync();
+    }
+    T.sync();   // no CTA leaves while another may still read its shared memory
 }
 
 namespace {
@@ -125,7 +184,16 @@ BatchKernel pick(int tpb, bool mixed) {
     }
 }
 
-int g_tuned_tpb = 0;   // process-wide choice of the autotuner (0: default 256)
+BatchKernel pick_cluster(bool mixed) { return mixed ? k_batch_cluster<256, 1> : k_batch_cluster<256, 0>; }
+
+// Launch shape of the batch kernel: threads per block and CTAs per
+// instance (1 = one block per instance, > 1 = a cluster per instance).
+struct BatchShape {
+    int tpb = 256;
+    int cluster = 1;
+};
+BatchShape g_tuned;          // process-wide choice of the autotuner
+bool g_have_tuned = false;
 
 double bytes_spmv(int64_t nnz, int64_t n, int sv, int sx) {
     return (double)nnz * (sv + 4) + 4.0 * (n + 1) + 2.0 * sx * n;
@@ -152,7 +220,7 @@ nn_status check_opts(const nn_solve_opts *o);
 
 // Runs the batch kernel; returns elapsed device milliseconds in *ms.
 static nn_status run_batch(int count, nn_system *const *systems, double *const *c, const nn_solve_opts *o,
-                           cudaStream_t st, int tpb, nn_solve_info *infos, float *ms_out) {
+                           cudaStream_t st, BatchShape shape, nn_solve_info *infos, float *ms_out) {
     const bool mixed = o->precision == NN_PREC_MIXED;
     if (o->solver != NN_SOLVER_GPCG || o->format != NN_FMT_SELL) {
         set_error("nn_batch_solve runs GPCG on the SELL format");
@@ -181,9 +249,11 @@ static nn_status run_batch(int count, nn_system *const *systems, double *const *
     S.st = st;
     double *d64;
     float *d32 = nullptr;
+    uint8_t *dfm;
     NN_TRY(S.a.alloc(&d64, w64, st));
     if (mixed) NN_TRY(S.a.alloc(&d32, w32, st));
-    size_t o64 = 0, o32 = 0;
+    NN_TRY(S.a.alloc(&dfm, w64 / 10, st));
+    size_t o64 = 0, o32 = 0, ofm = 0;
     for (int i = 0; i < count; ++i) {
         const nn_system *s = systems[i];
         BatchInst &b = h[i];
@@ -208,6 +278,8 @@ static nn_status run_batch(int count, nn_system *const *systems, double *const *
         b.c = c[i];
         b.w64 = d64 + o64;
         o64 += (size_t)10 * s->NF;
+        b.fm = dfm + ofm;
+        ofm += (size_t)s->NF;
         if (mixed) {
             b.w32 = d32 + o32;
             o32 += (size_t)12 * s->NF;
@@ -249,18 +321,51 @@ static nn_status run_batch(int count, nn_system *const *systems, double *const *
     if (const char *e = getenv("NNQP_CG_BOUND_STOP")) ctl.cg_bound_stop = atoi(e);
     if (const char *e = getenv("NNQP_GP_MAX")) ctl.gp_max = atoi(e);
     if (const char *e = getenv("NNQP_ETA2")) ctl.eta2 = atof(e);
-    BatchKernel k = pick(tpb, mixed);
-    int per = 0, dev = 0, sms = 0;
+    int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, tpb, 0);
-    const int grid = std::max(1, std::min(count, std::max(per, 1) * sms));
     cudaEvent_t e0, e1;
     NN_CUDA_TRY(cudaEventCreate(&e0));
     NN_CUDA_TRY(cudaEventCreate(&e1));
-    cudaEventRecord(e0, st);
-    (k<<<grid, tpb, 0, st>>>(dinst, dorder, count, dnext, ctl, o->rtol, o->inner_rtol, 200, dcnt, dsc),
-     count_launch());
+    const int tpb = shape.tpb;
+    if (shape.cluster <= 1) {
+        BatchKernel k = pick(tpb, mixed);
+        int per = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, tpb, 0);
+        const int grid = std::max(1, std::min(count, std::max(per, 1) * sms));
+        cudaEventRecord(e0, st);
+        (k<<<grid, tpb, 0, st>>>(dinst, dorder, count, dnext, ctl, o->rtol, o->inner_rtol, 200, dcnt, dsc),
+         count_launch());
+    } else {
+        BatchKernel k = pick_cluster(mixed);
+        const int C = shape.cluster;
+        if (C > 8) NN_CUDA_TRY(cudaFuncSetAttribute((const void *)k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = C;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.blockDim = dim3(256);
+        cfg.gridDim = dim3(C * std::max(1, sms / C));
+        cfg.dynamicSmemBytes = 0;
+        cfg.stream = st;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int nclusters = 0;
+        NN_CUDA_TRY(cudaOccupancyMaxActiveClusters(&nclusters, (const void *)k, &cfg));
+        if (nclusters < 1) {
+            set_error("nn_batch_solve: clusters of %d CTAs cannot be scheduled on this device", C);
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return NN_ERR_INVALID_ARG;
+        }
+        cfg.gridDim = dim3(C * std::min(count, nclusters));
+        cudaEventRecord(e0, st);
+        NN_CUDA_TRY(cudaLaunchKernelEx(&cfg, k, (const BatchInst *)dinst, (const int *)dorder, count, dnext, ctl,
+                                       o->rtol, o->inner_rtol, 200, dcnt, dsc));
+        count_launch();
+    }
     cudaEventRecord(e1, st);
     std::vector<int64_t> hc((size_t)count * kBatchCounters);
     std::vector<double> hs((size_t)2 * count);
@@ -316,8 +421,17 @@ nn_status nn_batch_solve(int count, nn_system *const *systems, double *const *c,
         set_error("nn_batch_solve: count >= 1 and arrays are required");
         return NN_ERR_INVALID_ARG;
     }
-    const int tpb = g_tuned_tpb ? g_tuned_tpb : 256;
-    return run_batch(count, systems, c, o, (cudaStream_t)stream, tpb, infos, nullptr);
+    BatchShape shape;
+    if (g_have_tuned) shape = g_tuned;
+    // NNQP_BATCH_SHAPE="<threads>x<ctas>" overrides the shape (tests, sweeps)
+    if (const char *e = getenv("NNQP_BATCH_SHAPE")) {
+        int t = 0, c = 0;
+        if (sscanf(e, "%dx%d", &t, &c) == 2 && (t == 128 || t == 256 || t == 512) && c >= 1 && c <= 16) {
+            shape.tpb = c > 1 ? 256 : t;
+            shape.cluster = c;
+        }
+    }
+    return run_batch(count, systems, c, o, (cudaStream_t)stream, shape, infos, nullptr);
 }
 
 nn_status nn_batch_autotune(int count, nn_system *const *systems, const nn_solve_opts *o, void *stream,
@@ -332,40 +446,39 @@ nn_status nn_batch_autotune(int count, nn_system *const *systems, const nn_solve
         return NN_ERR_INVALID_ARG;
     }
     cudaStream_t st = (cudaStream_t)stream;
-    // a sample of up to 64 instances, each solved for a short fixed budget of
-    // products from zero; the shape with the most products per second wins
-    const int ns = std::min(count, 64);
-    std::vector<nn_system *> sample(ns);
-    for (int i = 0; i < ns; ++i) sample[i] = systems[(int64_t)i * count / ns];
+    // The batch's makespan is set by its largest, slowest instances: every
+    // candidate shape solves the whole batch (at most 256 instances, largest
+    // first) under a cap of 1500 products per instance, and the shape with the
+    // shortest elapsed time wins.
+    std::vector<nn_system *> sample(systems, systems + count);
+    std::stable_sort(sample.begin(), sample.end(),
+                     [](const nn_system *a, const nn_system *b) { return a->nnzF > b->nnzF; });
+    if ((int)sample.size() > 256) sample.resize(256);
+    const int ns = (int)sample.size();
     Scratch S;
     S.st = st;
     std::vector<double *> cs(ns);
-    for (int i = 0; i < ns; ++i) {
-        NN_TRY(S.a.alloc(&cs[i], sample[i]->N, st));
-    }
+    for (int i = 0; i < ns; ++i) NN_TRY(S.a.alloc(&cs[i], sample[i]->N, st));
     nn_solve_opts t = *o;
-    t.max_iter = 120;
-    const int cands[3] = {128, 256, 512};
-    double best = -1.0;
-    int best_tpb = 256;
+    t.max_iter = 1500;
+    const BatchShape cands[6] = {{128, 1}, {256, 1}, {512, 1}, {256, 4}, {256, 8}, {256, 16}};
+    float best = 1e30f;
+    BatchShape pick_shape;
     std::vector<nn_solve_info> inf(ns);
-    for (int rep = 0; rep < 2; ++rep) {
-        for (int cidx = 0; cidx < 3; ++cidx) {
-            for (int i = 0; i < ns; ++i) NN_CUDA_TRY(cudaMemsetAsync(cs[i], 0, sizeof(double) * sample[i]->N, st));
-            float ms = 0.0f;
-            nn_status r = run_batch(ns, sample.data(), cs.data(), &t, st, cands[cidx], inf.data(), &ms);
-            if (r != NN_OK && r != NN_ERR_NOT_CONVERGED) return r;
-            double work = 0.0;
-            for (int i = 0; i < ns; ++i) work += (double)inf[i].spmv * (double)sample[i]->nnzF;
-            const double rate = work / std::max(ms, 1e-3f);
-            if (rep == 1 && rate > best) {
-                best = rate;
-                best_tpb = cands[cidx];
-            }
+    for (const BatchShape &sh : cands) {
+        for (int i = 0; i < ns; ++i) NN_CUDA_TRY(cudaMemsetAsync(cs[i], 0, sizeof(double) * sample[i]->N, st));
+        float ms = 0.0f;
+        nn_status r = run_batch(ns, sample.data(), cs.data(), &t, st, sh, inf.data(), &ms);
+        if (r == NN_ERR_INVALID_ARG) continue;   // shape not schedulable here
+        if (r != NN_OK && r != NN_ERR_NOT_CONVERGED) return r;
+        if (ms < best) {
+            best = ms;
+            pick_shape = sh;
         }
     }
-    g_tuned_tpb = best_tpb;
-    if (best_threads) *best_threads = best_tpb;
+    g_tuned = pick_shape;
+    g_have_tuned = true;
+    if (best_threads) *best_threads = pick_shape.tpb * 100 + pick_shape.cluster;
     clear_error();
     return NN_OK;
 }

@@ -22,7 +22,9 @@
 // reduction, so all threads take the same branches.  Per-thread partial sums
 // are kept in the vector type V (FP32 in the mixed-precision inner solves,
 // where FP64 arithmetic would cost 59x more per operation) and enter the
-// FP64 team reduction once per pass.
+// FP64 team reduction once per pass.  The face of a CG phase is kept as a
+// byte mask, so the CG iterations make no floating-point comparisons (on
+// GB300 FP64 compares run on the same narrow pipe as FP64 FMAs).
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -76,6 +78,7 @@ struct GpcgVecs {
     V *x, *g, *p, *q, *r, *z, *s, *w, *gw;
     const V *b;
     const V *dinv;
+    uint8_t *fm;          // face mask of the current CG phase (1 = free)
 };
 
 struct GpcgCtl {
@@ -92,17 +95,20 @@ struct GpcgCtl {
                          // 0: run CG to its stall test, the projected search clips
 };
 
-// vec counts vector streams (one read or write of an n-vector) made by the
-// passes beyond the gathered input and the output of each product; the
-// algorithmic traffic of a call is spmv * B_spmv + vec * n * sizeof(V).
+// vec counts vector streams (one read or write of an n-vector) and fl the
+// arithmetic operations per row made by the passes beyond the products; the
+// algorithmic traffic of a call is spmv * B_spmv + vec * n * sizeof(V), its
+// algorithmic operations spmv * 2 nnz + fl * n.
 struct GpcgStats {
-    int64_t spmv = 0, cg = 0, phases = 0, vec = 0;
+    int64_t spmv = 0, cg = 0, phases = 0, vec = 0, fl = 0;
     double gp2 = 0.0;
 };
 
 // Runs GPCG from the iterate in v.x (projected first).  On exit v.x holds
 // the final iterate, v.g its gradient (pointers may have been swapped).
-template <class Team, class Op, typename V>
+// CGV >= 0 fixes the CG variant at compile time (one body per kernel);
+// CGV = -1 reads it from C.cg_variant.
+template <class Team, class Op, typename V, int CGV = -1>
 __device__ int gpcg_solve(Team &T, const Rows &R, const Op &A, const Bounds<V> &B, GpcgVecs<V> &v,
                           const GpcgCtl &C, GpcgStats &st) {
     const double tol2 = C.tol * C.tol, ftol2 = C.face_tol * C.face_tol;
@@ -122,6 +128,7 @@ __device__ int gpcg_solve(Team &T, const Rows &R, const Op &A, const Bounds<V> &
         if (!team_sum(T, a, d)) return ST_TIMEOUT;
         ++st.spmv;
         st.vec += 1;
+        st.fl += 3;
         st.gp2 = d[0];
     }
     int status = ST_NOT_CONVERGED;
@@ -144,6 +151,7 @@ __device__ int gpcg_solve(Team &T, const Rows &R, const Op &A, const Bounds<V> &
                 A.apply(R, v.p, [&](int64_t i, V ap) { a1[0] += v.p[i] * ap; });
                 if (!team_sum(T, a1, d1)) return ST_TIMEOUT;
                 ++st.spmv;
+                st.fl += 2;
                 if (!(d1[0] > 0.0)) break;
                 alpha = st.gp2 / d1[0];
             }
@@ -174,6 +182,7 @@ __device__ int gpcg_solve(Team &T, const Rows &R, const Op &A, const Bounds<V> &
                 if (!team_sum(T, a2, d2)) return ST_TIMEOUT;
                 ++st.spmv;
                 st.vec += 7;
+                st.fl += 17;
                 if (0.5 * d2[2] <= C.mu * d2[0]) {
                     accepted = true;
                     break;
@@ -195,14 +204,16 @@ __device__ int gpcg_solve(Team &T, const Rows &R, const Op &A, const Bounds<V> &
         }
         if (st.gp2 <= tol2 || st.spmv >= C.max_spmv || !isfinite(st.gp2)) continue;
         // ------------------------------------------------ CG on faces
+        const bool count_cross = C.cg_bound_stop != 0;
         for (;;) {
-            if (C.cg_variant == 1) {
+            if ((CGV >= 0 ? CGV : C.cg_variant) == 1) {
                 // Chronopoulos-Gear form: one fused reduction per iteration
                 // (gamma = r'u and delta = w'u with u = D^-1 r, w = A_F u), the
                 // product A p carried by the recurrence q = w + beta q.
                 R.each([&](int64_t i) {
                     V xi = v.x[i];
-                    bool fr = xi > B.l(i) && xi < B.h(i);
+                    const bool fr = xi > B.l(i) && xi < B.h(i);
+                    v.fm[i] = fr ? 1 : 0;
                     V ri = fr ? -v.g[i] : zero;
                     v.r[i] = ri;
                     v.z[i] = v.dinv[i] * ri;
@@ -211,12 +222,12 @@ __device__ int gpcg_solve(Team &T, const Rows &R, const Op &A, const Bounds<V> &
                     v.q[i] = zero;
                 });
                 st.vec += 8;
+                st.fl += 1;
                 if (!T.sync()) return ST_TIMEOUT;
                 V a3[2] = {zero, zero};
                 double d3[2];
                 A.apply(R, v.z, [&](int64_t i, V au) {
-                    V xi = v.x[i];
-                    V wi = (xi > B.l(i) && xi < B.h(i)) ? au : zero;
+                    V wi = v.fm[i] ? au : zero;
                     v.w[i] = wi;
                     V ui = v.z[i];
                     a3[0] += v.r[i] * ui;
@@ -225,6 +236,7 @@ __device__ int gpcg_solve(Team &T, const Rows &R, const Op &A, const Bounds<V> &
                 if (!team_sum(T, a3, d3)) return ST_TIMEOUT;
                 ++st.spmv;
                 st.vec += 3;
+                st.fl += 4;
                 double gamma = d3[0], delta = d3[1];
                 if (!(gamma > 0.0) || !(delta > 0.0)) break;
                 double alpha = gamma / delta, beta = 0.0, maxdec = 0.0;
@@ -242,14 +254,16 @@ __device__ int gpcg_solve(Team &T, const Rows &R, const Op &A, const Bounds<V> &
                         v.s[i] = si;
                         v.r[i] = ri;
                         v.z[i] = v.dinv[i] * ri;
-                        V xs = v.x[i] + si;
-                        a4[3] += (xs < B.l(i) || xs > B.h(i)) ? one : zero;
+                        if (count_cross) {
+                            V xs = v.x[i] + si;
+                            a4[3] += (xs < B.l(i) || xs > B.h(i)) ? one : zero;
+                        }
                     });
-                    st.vec += 13;
+                    st.vec += count_cross ? 13 : 12;
+                    st.fl += 9;
                     if (!T.sync()) return ST_TIMEOUT;
                     A.apply(R, v.z, [&](int64_t i, V au) {
-                        V xi = v.x[i];
-                        V wi = (xi > B.l(i) && xi < B.h(i)) ? au : zero;
+                        V wi = v.fm[i] ? au : zero;
                         v.w[i] = wi;
                         V ri = v.r[i], ui = v.z[i];
                         a4[0] += ri * ui;
@@ -260,10 +274,11 @@ __device__ int gpcg_solve(Team &T, const Rows &R, const Op &A, const Bounds<V> &
                     ++st.spmv;
                     ++st.cg;
                     st.vec += 3;
+                    st.fl += 6;
                     const double dec = 0.5 * alpha * gamma;
                     if (dec > maxdec) maxdec = dec;
                     const double gnew = d4[0];
-                    if ((C.cg_bound_stop && d4[3] > 0.0) || dec <= C.eta2 * maxdec || d4[2] <= ftol2 ||
+                    if ((count_cross && d4[3] > 0.0) || dec <= C.eta2 * maxdec || d4[2] <= ftol2 ||
                         st.spmv >= C.max_spmv || !(gnew > 0.0))
                         break;
                     beta = gnew / gamma;
@@ -278,7 +293,8 @@ __device__ int gpcg_solve(Team &T, const Rows &R, const Op &A, const Bounds<V> &
                 double d3[1];
                 R.each([&](int64_t i) {
                     V xi = v.x[i];
-                    bool fr = xi > B.l(i) && xi < B.h(i);
+                    const bool fr = xi > B.l(i) && xi < B.h(i);
+                    v.fm[i] = fr ? 1 : 0;
                     V ri = fr ? -v.g[i] : zero;
                     V zi = v.dinv[i] * ri;
                     v.r[i] = ri;
@@ -288,7 +304,8 @@ __device__ int gpcg_solve(Team &T, const Rows &R, const Op &A, const Bounds<V> &
                     a3[0] += ri * zi;
                 });
                 if (!team_sum(T, a3, d3)) return ST_TIMEOUT;
-                st.vec += 7;
+                st.vec += 8;
+                st.fl += 3;
                 double rho = d3[0];
                 if (!(rho > 0.0)) break;
                 double maxdec = 0.0;
@@ -296,14 +313,14 @@ __device__ int gpcg_solve(Team &T, const Rows &R, const Op &A, const Bounds<V> &
                     V a4[1] = {zero};
                     double d4[1];
                     A.apply(R, v.p, [&](int64_t i, V ap) {
-                        V xi = v.x[i];
-                        V qi = (xi > B.l(i) && xi < B.h(i)) ? ap : zero;
+                        V qi = v.fm[i] ? ap : zero;
                         v.q[i] = qi;
                         a4[0] += v.p[i] * qi;
                     });
                     if (!team_sum(T, a4, d4)) return ST_TIMEOUT;
                     ++st.spmv;
-                    st.vec += 1;
+                    st.vec += 2;
+                    st.fl += 2;
                     if (!(d4[0] > 0.0)) break;
                     const double alpha = rho / d4[0];
                     const V va = (V)alpha;
@@ -318,21 +335,25 @@ __device__ int gpcg_solve(Team &T, const Rows &R, const Op &A, const Bounds<V> &
                         v.z[i] = zi;
                         a5[0] += ri * zi;
                         a5[1] += ri * ri;
-                        V xs = v.x[i] + si;
-                        a5[2] += (xs < B.l(i) || xs > B.h(i)) ? one : zero;
+                        if (count_cross) {
+                            V xs = v.x[i] + si;
+                            a5[2] += (xs < B.l(i) || xs > B.h(i)) ? one : zero;
+                        }
                     });
                     if (!team_sum(T, a5, d5)) return ST_TIMEOUT;
                     ++st.cg;
-                    st.vec += 9;
+                    st.vec += count_cross ? 9 : 8;
+                    st.fl += 9;
                     const double dec = 0.5 * alpha * rho;
                     if (dec > maxdec) maxdec = dec;
-                    if ((C.cg_bound_stop && d5[2] > 0.0) || dec <= C.eta2 * maxdec || d5[1] <= ftol2 ||
+                    if ((count_cross && d5[2] > 0.0) || dec <= C.eta2 * maxdec || d5[1] <= ftol2 ||
                         st.spmv >= C.max_spmv || !(d5[0] > 0.0))
                         break;
                     const V vb = (V)(d5[0] / rho);
                     rho = d5[0];
                     R.each([&](int64_t i) { v.p[i] = v.z[i] + vb * v.p[i]; });
                     st.vec += 3;
+                    st.fl += 2;
                     if (!T.sync()) return ST_TIMEOUT;
                 }
             }
@@ -362,6 +383,7 @@ __device__ int gpcg_solve(Team &T, const Rows &R, const Op &A, const Bounds<V> &
                 if (!team_sum(T, a6, d6)) return ST_TIMEOUT;
                 ++st.spmv;
                 st.vec += 7;
+                st.fl += 11;
                 if (0.5 * d6[2] <= C.mu * d6[0]) {
                     accepted = true;
                     break;

@@ -27,10 +27,11 @@ __host__ __device__ __forceinline__ int64_t inner_product_cap(int64_t n) {
 
 struct MixedStats {
     int64_t spmv64 = 0, spmv32 = 0, cg = 0, phases = 0, refinements = 0, vec64 = 0, vec32 = 0, fallback = 0;
+    int64_t fl64 = 0, fl32 = 0;
     double gp2 = 0.0;
 };
 
-template <class Team, class Op64, class Op32>
+template <int CGV, class Team, class Op64, class Op32>
 __device__ int mixed_solve(Team &T, const Rows &R, const Op64 &A, const Op32 &A32, double lo, double hi,
                            const double *b, double *x, GpcgVecs<float> &v, float *r32, float *l32, float *h32,
                            GpcgVecs<double> &v64, double tol, double inner_rtol, int max_ref, int64_t max_spmv,
@@ -55,6 +56,7 @@ __device__ int mixed_solve(Team &T, const Rows &R, const Op64 &A, const Op32 &A3
         ++st.spmv64;
         st.vec64 += 1;
         st.vec32 += 4;
+        st.fl64 += 5;
         st.gp2 = a[0];
         if (!isfinite(st.gp2)) return ST_NUMERIC;
         if (st.gp2 <= tol * tol) return ST_OK;
@@ -68,11 +70,12 @@ __device__ int mixed_solve(Team &T, const Rows &R, const Op64 &A, const Op32 &A3
             c.max_spmv = max_spmv - st.spmv64 - st.spmv32;
             GpcgStats gs;
             v64.x = x;
-            const int s = gpcg_solve(T, R, A, Bounds<double>{lo, hi, nullptr, nullptr}, v64, c, gs);
+            const int s = gpcg_solve<Team, Op64, double, CGV>(T, R, A, Bounds<double>{lo, hi, nullptr, nullptr}, v64, c, gs);
             st.spmv64 += gs.spmv;
             st.cg += gs.cg;
             st.phases += gs.phases;
             st.vec64 += gs.vec;
+            st.fl64 += gs.fl;
             st.gp2 = gs.gp2;
             if (s == ST_TIMEOUT) return s;
             if (v64.x != x) {
@@ -94,15 +97,17 @@ __device__ int mixed_solve(Team &T, const Rows &R, const Op64 &A, const Op32 &A3
         if (c.max_spmv > inner_cap) c.max_spmv = inner_cap;
         GpcgStats is;
         Bounds<float> B{0.0, 0.0, l32, h32};
-        int s = gpcg_solve(T, R, A32, B, v, c, is);
+        int s = gpcg_solve<Team, Op32, float, CGV>(T, R, A32, B, v, c, is);
         st.spmv32 += is.spmv;
         st.cg += is.cg;
         st.phases += is.phases;
         st.vec32 += is.vec;
+        st.fl32 += is.fl;
         if (s == ST_TIMEOUT || s == ST_NUMERIC) return s;
         R.each([&](int64_t i) { x[i] = clampv(x[i] + (double)v.x[i], lo, hi); });
         st.vec64 += 2;
         st.vec32 += 1;
+        st.fl64 += 1;
         if (!T.sync()) return ST_TIMEOUT;
     }
 }

@@ -15,7 +15,7 @@
 namespace nnqp {
 
 constexpr int kSolveThreads = 256;
-constexpr int kCounters = 12;   // per-step int64 counters written by the kernel
+constexpr int kCounters = 14;   // per-step int64 counters written by the kernel
 constexpr int kScalars = 4;     // per-step double results
 
 enum { MODE_STEADY = 0, MODE_TRANSIENT = 1, MODE_MIXED = 2 };
@@ -51,7 +51,24 @@ struct GridArgs {
     double *S, *Y;          // (m+1) slots of n doubles each
     int m;
     double h0;
+    // transient: initial iterate of step n+1 is P(2 c^(n) - c^(n-1)) when set
+    int predict;
+    double *xprev;          // [n] c^(n-1) at the free nodes
+    uint8_t *fmask;         // [n] face mask of the CG phases
 };
+
+// Initial iterate of a backward-Euler step: linear extrapolation of the last
+// two states, projected onto the box (the QP itself is unchanged; only the
+// starting point of its iteration moves).
+template <class Team>
+__device__ void transient_predict(const Rows &R, const GridArgs &a, double *x, int step) {
+    if (!a.predict) return;
+    R.each([&](int64_t i) {
+        const double xn = x[i];
+        if (step > 0) x[i] = clampv(xn + (xn - a.xprev[i]), a.lo, a.hi);
+        a.xprev[i] = xn;
+    });
+}
 
 // b of one backward-Euler step: b0 + M x / dt (Sec. 2.2.2, with c^(n));
 // returns ||b||_2 through den.
@@ -98,8 +115,8 @@ __device__ bool step_outputs(Team &T, const Rows &R, const GridArgs &a, const do
 
 // One instantiation per (format, mode) so that each kernel carries only the
 // code of its own path (register allocation is per kernel).
-template <int FMT, int MODE>
-__global__ void __launch_bounds__(kSolveThreads) k_solve_grid(GridArgs a) {
+template <int FMT, int MODE, int CGV>
+__global__ void __launch_bounds__(kSolveThreads, 3) k_solve_grid(GridArgs a) {
     __shared__ RedSmem sm;
     GridTeam T{a.bar, a.partials, (int)gridDim.x + a.bar_extra, a.timeout_ns, 0, 0, &sm};
     const Rows R = rows_of_block(a.n, a.nslices, blockIdx.x, gridDim.x);
@@ -115,15 +132,17 @@ __global__ void __launch_bounds__(kSolveThreads) k_solve_grid(GridArgs a) {
         if (MODE == MODE_TRANSIENT) {
             if (!transient_rhs(T, R, a, x, b, den)) return;
             cnt[1] += 1;   // products with M (FP64)
+            cnt[12] += 4;
+            transient_predict<GridTeam>(R, a, x, step);   // own rows; the solve's first pass syncs
         }
         if (!(den > 0.0)) den = a.den_fallback;
         if (MODE == MODE_MIXED) {
             GpcgVecs<float> v{a.v32[0], a.v32[1], a.v32[2], a.v32[3], a.v32[4], a.v32[5],
-                              a.v32[6], a.v32[7], a.v32[8], a.v32[9], a.dinv32};
+                              a.v32[6], a.v32[7], a.v32[8], a.v32[9], a.dinv32, a.fmask};
             GpcgVecs<double> v64{x, a.v64[1], a.v64[2], a.v64[3], a.v64[4], a.v64[5],
-                                 a.v64[6], a.v64[7], a.v64[8], b, a.dinv64};
+                                 a.v64[6], a.v64[7], a.v64[8], b, a.dinv64, a.fmask};
             MixedStats ms;
-            status = mixed_solve(T, R, a.A, a.A32, a.lo, a.hi, b, x, v, a.v32[9], a.v32[10], a.v32[11], v64,
+            status = mixed_solve<CGV>(T, R, a.A, a.A32, a.lo, a.hi, b, x, v, a.v32[9], a.v32[10], a.v32[11], v64,
                                  a.rtol * den, a.inner_rtol, a.max_ref, a.ctl.max_spmv,
                                  inner_product_cap(a.n), a.ctl, a.ctl, ms);
             if (status == ST_TIMEOUT) return;
@@ -135,16 +154,20 @@ __global__ void __launch_bounds__(kSolveThreads) k_solve_grid(GridArgs a) {
             cnt[6] = ms.vec64;
             cnt[7] = ms.vec32;
             cnt[11] = ms.fallback;
+            cnt[12] += ms.fl64;
+            cnt[13] += ms.fl32;
             gp2 = ms.gp2;
         } else {
             GpcgVecs<double> v{x, a.v64[1], a.v64[2], a.v64[3], a.v64[4], a.v64[5],
-                               a.v64[6], a.v64[7], a.v64[8], b, a.dinv64};
+                               a.v64[6], a.v64[7], a.v64[8], b, a.dinv64, a.fmask};
             GpcgCtl c = a.ctl;
             c.tol = a.rtol * den;
             c.face_tol = 0.5 * c.tol;
             GpcgStats gs;
-            if (FMT == 0) status = gpcg_solve(T, R, a.A, Bounds<double>{a.lo, a.hi, nullptr, nullptr}, v, c, gs);
-            else status = gpcg_solve(T, R, a.Acsr, Bounds<double>{a.lo, a.hi, nullptr, nullptr}, v, c, gs);
+            if (FMT == 0)
+                status = gpcg_solve<GridTeam, SellF64, double, CGV>(T, R, a.A, Bounds<double>{a.lo, a.hi, nullptr, nullptr}, v, c, gs);
+            else
+                status = gpcg_solve<GridTeam, CsrF64, double, CGV>(T, R, a.Acsr, Bounds<double>{a.lo, a.hi, nullptr, nullptr}, v, c, gs);
             if (status == ST_TIMEOUT) return;
             x = v.x;
             // keep the solution in slot 0 so that the next step starts there
@@ -157,6 +180,7 @@ __global__ void __launch_bounds__(kSolveThreads) k_solve_grid(GridArgs a) {
             cnt[3] = gs.cg;
             cnt[4] = gs.phases;
             cnt[6] = gs.vec;
+            cnt[12] += gs.fl;
             gp2 = gs.gp2;
         }
         if (!step_outputs(T, R, a, x, step, nsteps, status, cnt, gp2, den)) return;
@@ -179,6 +203,7 @@ __global__ void __launch_bounds__(kSolveThreads) k_lbfgs_grid(GridArgs a) {
         double *b = const_cast<double *>(a.b0);
         if (a.mode == MODE_TRANSIENT) {
             if (!transient_rhs(T, R, a, x0, b, den)) return;
+            transient_predict<GridTeam>(R, a, x0, step);
             cnt[1] += 1;
         }
         if (!(den > 0.0)) den = a.den_fallback;
@@ -345,6 +370,8 @@ void fill_info(const nn_system *s, const int64_t *cnt, const double *sc, int pre
     info->active_lo = cnt[8];
     info->active_hi = cnt[9];
     info->fp64_fallback = cnt[11];
+    info->flops64_algo = 2.0 * cnt[1] * (double)s->nnzF + (double)cnt[12] * s->NF;
+    info->flops_algo = info->flops64_algo + 2.0 * cnt[2] * (double)s->nnzF + (double)cnt[13] * s->NF;
     info->kkt_rel = std::sqrt(sc[0]) / sc[1];
     info->kkt_inf = NAN;
     info->objective = NAN;
@@ -399,6 +426,7 @@ nn_status run_grid(nn_system *s, const nn_solve_opts *o, int mode, int nsteps, c
     a.c_hist = c_hist;
     a.nsteps = nsteps;
     for (int k = 0; k < 10; ++k) NN_TRY(S.a.alloc(&a.v64[k], n, st));
+    NN_TRY(S.a.alloc(&a.fmask, n, st));
     if (mixed)
         for (int k = 0; k < 12; ++k) NN_TRY(S.a.alloc(&a.v32[k], n, st));
     a.ctl.max_spmv = o->max_iter;
@@ -432,11 +460,15 @@ nn_status run_grid(nn_system *s, const nn_solve_opts *o, int mode, int nsteps, c
         NN_TRY(S.a.alloc(&a.S, (size_t)(a.m + 1) * n, st));
         NN_TRY(S.a.alloc(&a.Y, (size_t)(a.m + 1) * n, st));
     }
-    void (*kern)(GridArgs) = lbfgs                   ? k_lbfgs_grid
-                             : fmt == NN_FMT_CSR     ? k_solve_grid<1, MODE_STEADY>
-                             : mode == MODE_MIXED    ? k_solve_grid<0, MODE_MIXED>
-                             : mode == MODE_TRANSIENT ? k_solve_grid<0, MODE_TRANSIENT>
-                                                     : k_solve_grid<0, MODE_STEADY>;
+    a.predict = o->extrapolate;
+    if (mode == MODE_TRANSIENT && a.predict) NN_TRY(S.a.alloc(&a.xprev, n, st));
+    const bool cg2 = a.ctl.cg_variant == 1;
+    void (*kern)(GridArgs) =
+        lbfgs                    ? k_lbfgs_grid
+        : fmt == NN_FMT_CSR      ? (cg2 ? k_solve_grid<1, MODE_STEADY, 1> : k_solve_grid<1, MODE_STEADY, 0>)
+        : mode == MODE_MIXED     ? (cg2 ? k_solve_grid<0, MODE_MIXED, 1> : k_solve_grid<0, MODE_MIXED, 0>)
+        : mode == MODE_TRANSIENT ? (cg2 ? k_solve_grid<0, MODE_TRANSIENT, 1> : k_solve_grid<0, MODE_TRANSIENT, 0>)
+                                 : (cg2 ? k_solve_grid<0, MODE_STEADY, 1> : k_solve_grid<0, MODE_STEADY, 0>);
     const int maxg = max_coresident(kern);
     // one slice per warp at least; grids of up to one block per SM while that
     // covers the rows in a few slices per warp (fewer barrier arrivals), the
@@ -663,7 +695,10 @@ int mode_for(const nn_system *s, const nn_solve_opts *o) {
 
 // Co-resident blocks of the steady/mixed solve kernel on the current device.
 int solve_grid_capacity() {
-    return std::min(max_coresident(k_solve_grid<0, MODE_STEADY>), max_coresident(k_solve_grid<0, MODE_MIXED>));
+    int c = max_coresident(k_solve_grid<0, MODE_STEADY, 0>);
+    c = std::min(c, max_coresident(k_solve_grid<0, MODE_STEADY, 1>));
+    c = std::min(c, max_coresident(k_solve_grid<0, MODE_MIXED, 0>));
+    return std::min(c, max_coresident(k_solve_grid<0, MODE_MIXED, 1>));
 }
 
 // One steady solve with a fixed persistent grid (serving).

@@ -174,6 +174,57 @@ struct GridTeam {
     }
 };
 
+// The CTAs of one thread-block cluster (all co-scheduled by the hardware).
+// Barriers are the hardware cluster barrier; a reduction writes each CTA's
+// block sum to its own shared memory, and after the cluster barrier every
+// CTA reads all of them through distributed shared memory in rank order, so
+// all CTAs obtain the same bits.  Two exchange slots alternate: a CTA can
+// only overwrite slot s after every CTA has passed the barrier that follows
+// its last read of s.
+struct ClusterTeam {
+    RedSmem *sm;
+    double *xch;                  // this CTA's [2][kMaxRed] exchange buffer (shared memory)
+    unsigned rank, size;
+    int slot;
+
+    __device__ __forceinline__ static void cluster_barrier() {
+        asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::
+                         : "memory");
+    }
+    __device__ __forceinline__ bool sync() {
+        cluster_barrier();
+        return true;
+    }
+    template <int K>
+    __device__ bool reduce(double (&v)[K]) {
+        block_sum<K>(v, *sm);
+        slot ^= 1;
+        double *mine = xch + slot * kMaxRed;
+        if (threadIdx.x == 0)
+#pragma unroll
+            for (int k = 0; k < K; ++k) mine[k] = v[k];
+        cluster_barrier();
+        if (threadIdx.x < K) {
+            const int k = threadIdx.x;
+            const uint32_t local = (uint32_t)__cvta_generic_to_shared(mine + k);
+            double t = 0.0;
+            for (unsigned r = 0; r < size; ++r) {
+                uint32_t remote;
+                asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(local), "r"(r));
+                double x;
+                asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(x) : "r"(remote) : "memory");
+                t += x;
+            }
+            sm->bcast[k] = t;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < K; ++k) v[k] = sm->bcast[k];
+        __syncthreads();
+        return true;
+    }
+};
+
 // Rows owned by a block: the SELL slices [s0, s1); warp w of the block
 // takes slices s0 + w, s0 + w + nwarps, ...; lane l takes row 32 s + l.
 struct Rows {

@@ -230,13 +230,16 @@ def test_not_converged_returns_feasible_iterate():
 
 # ------------------------------------------------------------------ transient
 
-def test_transient_small_matches_oracle_trajectory():
+@pytest.mark.parametrize("extrapolate", [0, 1])
+def test_transient_small_matches_oracle_trajectory(extrapolate):
+    """Either first iterate (c^(n), or the projected extrapolation
+    2 c^(n) - c^(n-1)) reaches the oracle's step solution."""
     spec = I.config2_transient_3d(n=10, nsteps=8)
     s = gpu_system(spec)
     c0 = torch.tensor(spec.c0, device=DEV)
     cf = torch.zeros_like(c0)
     hist = torch.zeros(spec.nsteps * spec.n_nodes, dtype=torch.float64, device=DEV)
-    infos = P.nn_transient(s, c0, spec.nsteps, cf, hist, P.solve_opts(rtol=1e-11))
+    infos = P.nn_transient(s, c0, spec.nsteps, cf, hist, P.solve_opts(rtol=1e-11, extrapolate=extrapolate))
     assert all(i["status"] == 0 for i in infos)
     H = hist.cpu().numpy().reshape(spec.nsteps, -1)
     assert np.array_equal(H[-1], cf.cpu().numpy())
@@ -264,7 +267,8 @@ def test_transient_step_api_equals_batched_steps():
         c = nxt
     cf = torch.zeros_like(c)
     hist = torch.zeros(3 * spec.n_nodes, dtype=torch.float64, device=DEV)
-    P.nn_transient(s, torch.tensor(spec.c0, device=DEV), 3, cf, hist)
+    # nn_step starts each QP from c^(n); so does nn_transient without extrapolation
+    P.nn_transient(s, torch.tensor(spec.c0, device=DEV), 3, cf, hist, P.solve_opts(extrapolate=0))
     H = hist.view(3, -1)
     for n in range(3):
         assert torch.equal(H[n], outs[n])

@@ -225,7 +225,10 @@ nn_status nn_step(nn_system *s, const double *c_prev, double *c_next, int memory
 /* nsteps backward-Euler steps from c0 in ONE device launch; writes the
  * final state to c_final [N] and, if c_hist != NULL, every state to
  * c_hist [nsteps][N].  infos: NULL or [nsteps] per-step records (time_ms
- * is reported on the first record only). */
+ * is reported on the first record only).  With precision NN_PREC_MIXED
+ * (system assembled with build_mixed = 1) every step's QP is solved by
+ * FP32 inner solves refined in FP64; the right-hand side, the stopping
+ * test and the stored states stay FP64. */
 nn_status nn_transient(nn_system *s, const double *c0, int nsteps, double *c_final, double *c_hist, int memory,
                        const nn_solve_opts *o, void *stream, nn_solve_info *infos);
 

@@ -11,7 +11,9 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libnnqp.so")
 OBJ = os.path.join(HERE, "_build")
 
-SOURCES = ["scan.cu", "assemble.cu", "solve.cu", "batch.cu", "serve.cpp", "capi.cpp"]
+SOURCES = ["scan.cu", "assemble.cu", "solve.cu", "solve_grid_steady.cu", "solve_grid_transient.cu",
+           "solve_grid_mixed.cu", "solve_grid_mixed_transient.cu", "batch.cu", "batch_fp64.cu", "batch_mixed.cu",
+           "serve.cpp", "capi.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 
@@ -53,7 +55,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
             sys.stderr.write(r.stderr)
         return obj
 
-    with ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
+    with ThreadPoolExecutor(max_workers=min(os.cpu_count() or 8, len(srcs))) as ex:
         objs = list(ex.map(compile_one, srcs))
     tmp = OUT + ".tmp"
     cmd = [nvcc()] + ARCH + ["-shared", "-o", tmp] + objs + ["-lpthread"]

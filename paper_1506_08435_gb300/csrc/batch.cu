@@ -1,9 +1,6 @@
-// Batched solves: many independent QPs of uneven size in ONE persistent
-// launch.  Every thread block takes the next instance (largest first) from
-// a device work counter and solves it alone with block-level barriers and
-// reductions, so no block ever waits on another.  The solver is the same
-// GPCG (and mixed-precision refinement) code as the single-system path,
-// instantiated for a one-block team.
+// Batched solves, host side: per-instance scratch, the launch shape (threads
+// per block x CTAs per instance), the autotuner and the per-instance records.
+// The kernels are in batch.cuh.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -12,179 +9,15 @@
 #include <numeric>
 #include <vector>
 #include "internal.h"
-#include "gpcg.cuh"
-#include "refine.cuh"
+#include "batch.cuh"
 
 namespace nnqp {
 
-struct BatchInst {
-    int64_t n, N, nslices;
-    const int64_t *sptr;
-    const int32_t *col;
-    const double *val;
-    const double *diag;
-    const double *dinv64;
-    const float *val32;
-    const float *rsum32;
-    const float *dinv32;
-    const double *b0;
-    const int32_t *free_node;
-    const uint8_t *dmask;
-    const double *dval;
-    double lo, hi, den;
-    double *c;          // full node vector: warm start in, solution out
-    double *w64;        // 10 n doubles
-    float *w32;         // 12 n floats (mixed)
-    uint8_t *fm;        // n bytes: face mask of the CG phases
-};
-
-constexpr int kBatchCounters = 9;
-
-// Solves instance `id` with team T; this CTA owns the rows R of it.
-template <int MIXED, class Team>
-__device__ void solve_instance(Team &T, const Rows &R, const BatchInst &I, int id, unsigned rank, unsigned size,
-                               const GpcgCtl &ctl, double rtol, double inner_rtol, int max_ref, int64_t *counters,
-                               double *scalars) {
-    const int64_t n = I.n;
-    double *x = I.w64;
-    R.each([&](int64_t i) { x[i] = I.c[I.free_node[i]]; });
-    if (!T.sync()) return;
-    const SellF64 A{n, I.nslices, I.sptr, I.col, I.val, I.diag};
-    int64_t cnt[kBatchCounters] = {0};
-    double gp2 = 0.0;
-    int status;
-    if (MIXED) {
-        float *w = I.w32;
-        GpcgVecs<float> v{w, w + n, w + 2 * n, w + 3 * n, w + 4 * n, w + 5 * n, w + 6 * n, w + 7 * n, w + 8 * n,
-                          w + 9 * n, I.dinv32, I.fm};
-        const SellF32Diff A32{n, I.nslices, I.sptr, I.col, I.val32, I.rsum32};
-        double *w6 = I.w64;
-        GpcgVecs<double> v64{x, w6 + n, w6 + 2 * n, w6 + 3 * n, w6 + 4 * n, w6 + 5 * n, w6 + 6 * n,
-                             w6 + 7 * n, w6 + 8 * n, I.b0, I.dinv64, I.fm};
-        MixedStats ms;
-        status = mixed_solve<0>(T, R, A, A32, I.lo, I.hi, I.b0, x, v, w + 9 * n, w + 10 * n, w + 11 * n, v64,
-                                rtol * I.den, inner_rtol, max_ref, ctl.max_spmv, inner_product_cap(n), ctl, ctl, ms);
-        cnt[1] = ms.spmv64;
-        cnt[2] = ms.spmv32;
-        cnt[3] = ms.cg;
-        cnt[4] = ms.phases;
-        cnt[5] = ms.refinements;
-        cnt[6] = ms.vec64;
-        cnt[7] = ms.vec32;
-        cnt[8] = ms.fallback;
-        gp2 = ms.gp2;
-    } else {
-        double *w = I.w64;
-        GpcgVecs<double> v{w, w + n, w + 2 * n, w + 3 * n, w + 4 * n, w + 5 * n, w + 6 * n, w + 7 * n,
-                           w + 8 * n, I.b0, I.dinv64, I.fm};
-        GpcgCtl c = ctl;
-        c.tol = rtol * I.den;
-        c.face_tol = 0.5 * c.tol;
-        GpcgStats gs;
-        status = gpcg_solve<Team, SellF64, double, 0>(T, R, A, Bounds<double>{I.lo, I.hi, nullptr, nullptr}, v, c, gs);
-        x = v.x;
-        cnt[1] = gs.spmv;
-        cnt[3] = gs.cg;
-        cnt[4] = gs.phases;
-        cnt[6] = gs.vec;
-        gp2 = gs.gp2;
-    }
-    R.each([&](int64_t i) { I.c[I.free_node[i]] = x[i]; });
-    for (int64_t v = (int64_t)rank * blockDim.x + threadIdx.x; v < I.N; v += (int64_t)size * blockDim.x)
-        if (I.dmask[v]) I.c[v] = I.dval[v];
-    if (rank == 0 && threadIdx.x == 0) {
-        cnt[0] = status;
-        for (int k = 0; k < kBatchCounters; ++k) counters[(int64_t)id * kBatchCounters + k] = cnt[k];
-        scalars[2 * id] = gp2;
-        scalars[2 * id + 1] = I.den;
-    }
-}
-
-// One thread block per instance.
-template <int TPB, int MIXED>
-__global__ void __launch_bounds__(TPB) k_batch(const BatchInst *__restrict__ insts, const int *__restrict__ order,
-                                               int count, unsigned *next, GpcgCtl ctl, double rtol,
-                                               double inner_rtol, int max_ref, int64_t *counters, double *scalars) {
-    __shared__ RedSmem sm;
-    __shared__ int s_q;
-    BlockTeam T{&sm};
-    for (;;) {
-        if (threadIdx.x == 0) s_q = (int)atomicAdd(next, 1u);
-        __syncthreads();
-        const int q = s_q;
-        __syncthreads();
-        if (q >= count) return;
-        const int id = order[q];
-        const BatchInst I = insts[id];
-        solve_instance<MIXED>(T, Rows{0, I.nslices, I.n}, I, id, 0, 1, ctl, rtol, inner_rtol, max_ref, counters,
-                              scalars);
-        __syncthreads();
-    }
-}
-
-__device__ __forceinline__ unsigned cluster_rank() {
-    unsigned r;
-    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-    return r;
-}
-__device__ __forceinline__ unsigned cluster_size() {
-    unsigned r;
-    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
-    return r;
-}
-
-// One thread-block cluster per instance: the instance's slices are split
-// over the cluster's CTAs (one per SM), barriers are the hardware cluster
-// barrier, reductions go through distributed shared memory.
-template <int TPB, int MIXED>
-__global__ void __launch_bounds__(TPB) k_batch_cluster(const BatchInst *__restrict__ insts,
-                                                       const int *__restrict__ order, int count, unsigned *next,
-                                                       GpcgCtl ctl, double rtol, double inner_rtol, int max_ref,
-                                                       int64_t *counters, double *scalars) {
-    __shared__ RedSmem sm;
-    __shared__ double xch[2 * kMaxRed];
-    __shared__ int s_q;
-    const unsigned rank = cluster_rank(), size = cluster_size();
-    ClusterTeam T{&sm, xch, rank, size, 0};
-    for (;;) {
-        if (rank == 0 && threadIdx.x == 0) s_q = (int)atomicAdd(next, 1u);
-        T.sync();
-        // every CTA reads the instance index taken by CTA 0
-        __shared__ int s_q0;
-        if (threadIdx.x == 0) {
-            const uint32_t local = (uint32_t)__cvta_generic_to_shared(&s_q);
-            uint32_t remote;
-            asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(local), "r"(0u));
-            int q;
-            asm volatile("ld.shared::cluster.s32 %0, [%1];" : "=r"(q) : "r"(remote) : "memory");
-            s_q0 = q;
-        }
-        T.sync();
-        const int q = s_q0;
-        if (q >= count) break;
-        const int id = order[q];
-        const BatchInst I = insts[id];
-        solve_instance<MIXED>(T, rows_of_block(I.n, I.nslices, (int)rank, (int)size), I, id, rank, size, ctl, rtol,
-                              inner_rtol, max_ref, counters, scalars);
-        T.sync();
-    }
-    T.sync();   // no CTA leaves while another may still read its shared memory
-}
-
 namespace {
 
-using BatchKernel = void (*)(const BatchInst *, const int *, int, unsigned *, GpcgCtl, double, double, int,
-                             int64_t *, double *);
-
-BatchKernel pick(int tpb, bool mixed) {
-    switch (tpb) {
-        case 128: return mixed ? k_batch<128, 1> : k_batch<128, 0>;
-        case 512: return mixed ? k_batch<512, 1> : k_batch<512, 0>;
-        default: return mixed ? k_batch<256, 1> : k_batch<256, 0>;
-    }
+BatchKernel pick_kernel(bool mixed, int tpb, int cluster, int cgv) {
+    return mixed ? batch_kernel_mixed(tpb, cluster, cgv) : batch_kernel_fp64(tpb, cluster, cgv);
 }
-
-BatchKernel pick_cluster(bool mixed) { return mixed ? k_batch_cluster<256, 1> : k_batch_cluster<256, 0>; }
 
 // Launch shape of the batch kernel: threads per block and CTAs per
 // instance (1 = one block per instance, > 1 = a cluster per instance).
@@ -242,8 +75,8 @@ static nn_status run_batch(int count, nn_system *const *systems, double *const *
             set_error("nn_batch_solve: system %d has no FP32 copy", i);
             return NN_ERR_INVALID_ARG;
         }
-        w64 += (size_t)10 * s->NF;
-        if (mixed) w32 += (size_t)12 * s->NF;
+        w64 += (size_t)11 * s->NF;
+        if (mixed) w32 += (size_t)13 * s->NF;
     }
     Scratch S;
     S.st = st;
@@ -252,7 +85,7 @@ static nn_status run_batch(int count, nn_system *const *systems, double *const *
     uint8_t *dfm;
     NN_TRY(S.a.alloc(&d64, w64, st));
     if (mixed) NN_TRY(S.a.alloc(&d32, w32, st));
-    NN_TRY(S.a.alloc(&dfm, w64 / 10, st));
+    NN_TRY(S.a.alloc(&dfm, w64 / 11, st));
     size_t o64 = 0, o32 = 0, ofm = 0;
     for (int i = 0; i < count; ++i) {
         const nn_system *s = systems[i];
@@ -277,12 +110,12 @@ static nn_status run_batch(int count, nn_system *const *systems, double *const *
         b.den = den_of(s);
         b.c = c[i];
         b.w64 = d64 + o64;
-        o64 += (size_t)10 * s->NF;
+        o64 += (size_t)11 * s->NF;
         b.fm = dfm + ofm;
         ofm += (size_t)s->NF;
         if (mixed) {
             b.w32 = d32 + o32;
-            o32 += (size_t)12 * s->NF;
+            o32 += (size_t)13 * s->NF;
         } else {
             b.w32 = nullptr;
         }
@@ -324,12 +157,17 @@ static nn_status run_batch(int count, nn_system *const *systems, double *const *
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int tpb = shape.cluster > 1 ? 256 : shape.tpb;
+    BatchKernel k = pick_kernel(mixed, tpb, shape.cluster, ctl.cg_variant);
+    if (!k) {
+        set_error("nn_batch_solve: no kernel for %d threads x %d CTAs, CG variant %d", tpb, shape.cluster,
+                  ctl.cg_variant);
+        return NN_ERR_INVALID_ARG;
+    }
     cudaEvent_t e0, e1;
     NN_CUDA_TRY(cudaEventCreate(&e0));
     NN_CUDA_TRY(cudaEventCreate(&e1));
-    const int tpb = shape.tpb;
     if (shape.cluster <= 1) {
-        BatchKernel k = pick(tpb, mixed);
         int per = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, tpb, 0);
         const int grid = std::max(1, std::min(count, std::max(per, 1) * sms));
@@ -337,7 +175,6 @@ static nn_status run_batch(int count, nn_system *const *systems, double *const *
         (k<<<grid, tpb, 0, st>>>(dinst, dorder, count, dnext, ctl, o->rtol, o->inner_rtol, 200, dcnt, dsc),
          count_launch());
     } else {
-        BatchKernel k = pick_cluster(mixed);
         const int C = shape.cluster;
         if (C > 8) NN_CUDA_TRY(cudaFuncSetAttribute((const void *)k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
         cudaLaunchConfig_t cfg = {};
@@ -426,7 +263,8 @@ nn_status nn_batch_solve(int count, nn_system *const *systems, double *const *c,
     // NNQP_BATCH_SHAPE="<threads>x<ctas>" overrides the shape (tests, sweeps)
     if (const char *e = getenv("NNQP_BATCH_SHAPE")) {
         int t = 0, c = 0;
-        if (sscanf(e, "%dx%d", &t, &c) == 2 && (t == 128 || t == 256 || t == 512) && c >= 1 && c <= 16) {
+        if (sscanf(e, "%dx%d", &t, &c) == 2 && (t == 128 || t == 256 || t == 512) && c >= 1 && c <= kMaxCluster &&
+            (c & (c - 1)) == 0) {
             shape.tpb = c > 1 ? 256 : t;
             shape.cluster = c;
         }

@@ -222,10 +222,6 @@ static nn_status solve_common(nn_system *s, const nn_solve_opts *o, int want_tra
         set_error("this system is transient (dt > 0): use nn_step or nn_transient");
         return NN_ERR_INVALID_ARG;
     }
-    if (want_transient && o->precision == NN_PREC_MIXED) {
-        set_error("mixed precision is available for steady systems");
-        return NN_ERR_INVALID_ARG;
-    }
     return solve_entry(s, o, mode_for(s, o), nsteps, c_in, c_out, c_hist, memory, S(stream), infos, ninfos);
 }
 

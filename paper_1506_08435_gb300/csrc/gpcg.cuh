@@ -73,12 +73,73 @@ __device__ __forceinline__ bool team_sum(Team &T, const V (&acc)[K], double (&ou
     return T.reduce(out);
 }
 
+// Team reduction followed by scalar work done once per block: f(sums, out)
+// runs on warp 0 only (its lanes compute identical values) and its M results
+// reach every thread through shared memory.  On GB300 every FP64 warp
+// instruction occupies the SM's narrow FP64 pipe for many cycles, so a
+// scalar division repeated by all warps of a block costs as much as the
+// reduction itself.
+template <class Team, typename V, int K, int M, class F>
+__device__ __forceinline__ bool team_sum_scalar(Team &T, const V (&acc)[K], double (&out)[M], F &&f) {
+    double d[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) d[k] = (double)acc[k];
+    if (!T.reduce(d)) return false;
+    RedSmem &sm = *T.sm;
+    if ((threadIdx.x >> 5) == 0) {
+        double r[M];
+        f(d, r);
+        if ((threadIdx.x & 31) == 0)
+#pragma unroll
+            for (int j = 0; j < M; ++j) sm.sc[j] = r[j];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < M; ++j) out[j] = sm.sc[j];
+    __syncthreads();
+    return true;
+}
+
+__device__ __forceinline__ bool flag_set(double f) { return __double_as_longlong(f) != 0; }
+
+// Scalar step of the Chronopoulos-Gear / pipelined CG iterations: from the
+// sums d = (gamma', delta', r'r, crossings) and the current alpha, beta,
+// gamma, maxdec, decides whether the CG phase stops and computes the next
+// coefficients.  r = (stop, alpha, beta, gamma, maxdec).
+__device__ __forceinline__ void cg_scalar_step(const double (&d)[4], double (&r)[5], double alpha, double beta,
+                                               double gamma, double maxdec, double eta2, double ftol2,
+                                               bool count_cross) {
+    const double dec = 0.5 * alpha * gamma;
+    if (dec > maxdec) maxdec = dec;
+    const double gnew = d[0];
+    double stop = 0.0;
+    if ((count_cross && d[3] > 0.0) || dec <= eta2 * maxdec || d[2] <= ftol2 || !(gnew > 0.0)) {
+        stop = 1.0;
+    } else {
+        const double bnew = gnew / gamma;
+        const double den = d[1] - bnew * gnew / alpha;
+        if (!(den > 0.0)) {
+            stop = 1.0;
+        } else {
+            alpha = gnew / den;
+            beta = bnew;
+            gamma = gnew;
+        }
+    }
+    r[0] = stop;
+    r[1] = alpha;
+    r[2] = beta;
+    r[3] = gamma;
+    r[4] = maxdec;
+}
+
 template <typename V>
 struct GpcgVecs {
     V *x, *g, *p, *q, *r, *z, *s, *w, *gw;
     const V *b;
     const V *dinv;
     uint8_t *fm;          // face mask of the current CG phase (1 = free)
+    V *m2;                // second product input of the pipelined CG (variant 2)
 };
 
 struct GpcgCtl {
@@ -90,7 +151,9 @@ struct GpcgCtl {
     double eta1, eta2;   // stall ratios of the GP and CG phases
     double mu;           // Armijo constant
     int cg_variant;      // 0: textbook PCG (3 team barriers per iteration);
-                         // 1: Chronopoulos-Gear PCG (2 barriers, one fused reduction)
+                         // 1: Chronopoulos-Gear PCG (2 barriers, one fused reduction);
+                         // 2: pipelined PCG (1 barrier: product, updates and
+                         //    reduction in one pass; needs GpcgVecs::m2)
     int cg_bound_stop;   // 1: end the CG phase as soon as x + s leaves the box;
                          // 0: run CG to its stall test, the projected search clips
 };
@@ -243,7 +306,6 @@ __device__ int gpcg_solve(Team &T, const Rows &R, const Op &A, const Bounds<V> &
                 for (int k = 0; k < C.cg_max; ++k) {
                     const V va = (V)alpha, vb = (V)beta;
                     V a4[4] = {zero, zero, zero, zero};   // gamma, delta, r'r, bound crossings
-                    double d4[4];
                     R.each([&](int64_t i) {
                         V pi = v.z[i] + vb * v.p[i];
                         V qi = v.w[i] + vb * v.q[i];
@@ -270,22 +332,113 @@ __device__ int gpcg_solve(Team &T, const Rows &R, const Op &A, const Bounds<V> &
                         a4[1] += wi * ui;
                         a4[2] += ri * ri;
                     });
-                    if (!team_sum(T, a4, d4)) return ST_TIMEOUT;
+                    double o[5];
+                    if (!team_sum_scalar(T, a4, o, [&](const double (&d)[4], double (&r)[5]) {
+                            cg_scalar_step(d, r, alpha, beta, gamma, maxdec, C.eta2, ftol2, count_cross);
+                        }))
+                        return ST_TIMEOUT;
                     ++st.spmv;
                     ++st.cg;
                     st.vec += 3;
                     st.fl += 6;
-                    const double dec = 0.5 * alpha * gamma;
-                    if (dec > maxdec) maxdec = dec;
-                    const double gnew = d4[0];
-                    if ((count_cross && d4[3] > 0.0) || dec <= C.eta2 * maxdec || d4[2] <= ftol2 ||
-                        st.spmv >= C.max_spmv || !(gnew > 0.0))
-                        break;
-                    beta = gnew / gamma;
-                    const double den = d4[1] - beta * gnew / alpha;
-                    if (!(den > 0.0)) break;
-                    alpha = gnew / den;
-                    gamma = gnew;
+                    maxdec = o[4];
+                    if (flag_set(o[0]) || st.spmv >= C.max_spmv) break;
+                    alpha = o[1];
+                    beta = o[2];
+                    gamma = o[3];
+                }
+            } else if ((CGV >= 0 ? CGV : C.cg_variant) == 2) {
+                // Pipelined form (Ghysels & Vanroose, Parallel Comput. 40, 2014)
+                // with the Jacobi preconditioner applied explicitly: u = D^-1 r,
+                // m = D^-1 w, w = A_F u.  The product n = A_F m of iteration i
+                // only needs vectors of iteration i, so it is fused with every
+                // update of the iteration and with the partial dot products of
+                // the next one; the reduction's barrier also publishes m.  m is
+                // double-buffered (gw, m2): a pass reads m_i of other rows while
+                // writing m_(i+1) of its own.  Recurrences (q = A_F p via v.q,
+                // z = A_F D^-1 A_F p via v.z):
+                //   z = n + beta z, q = w + beta q, p = u + beta p,
+                //   s += alpha p, r -= alpha q, w -= alpha z.
+                V *mc = v.gw, *mn = v.m2;
+                R.each([&](int64_t i) {
+                    V xi = v.x[i];
+                    const bool fr = xi > B.l(i) && xi < B.h(i);
+                    v.fm[i] = fr ? 1 : 0;
+                    V ri = fr ? -v.g[i] : zero;
+                    v.r[i] = ri;
+                    mn[i] = v.dinv[i] * ri;    // u_0, input of the first product
+                    v.s[i] = zero;
+                    v.p[i] = zero;
+                    v.q[i] = zero;
+                    v.z[i] = zero;
+                });
+                st.vec += 10;
+                st.fl += 1;
+                if (!T.sync()) return ST_TIMEOUT;
+                V a3[2] = {zero, zero};
+                double d3[2];
+                A.apply(R, mn, [&](int64_t i, V au) {
+                    V wi = v.fm[i] ? au : zero;
+                    V di = v.dinv[i];
+                    v.w[i] = wi;
+                    mc[i] = di * wi;
+                    V ri = v.r[i], ui = di * ri;
+                    a3[0] += ri * ui;
+                    a3[1] += wi * ui;
+                });
+                if (!team_sum(T, a3, d3)) return ST_TIMEOUT;
+                ++st.spmv;
+                st.vec += 5;
+                st.fl += 6;
+                double gamma = d3[0], delta = d3[1];
+                if (!(gamma > 0.0) || !(delta > 0.0)) break;
+                double alpha = gamma / delta, beta = 0.0, maxdec = 0.0;
+                for (int k = 0; k < C.cg_max; ++k) {
+                    const V va = (V)alpha, vb = (V)beta;
+                    V a4[4] = {zero, zero, zero, zero};   // gamma, delta, r'r, bound crossings
+                    A.apply(R, mc, [&](int64_t i, V an) {
+                        V ni = v.fm[i] ? an : zero;
+                        V di = v.dinv[i];
+                        V ri = v.r[i], wi = v.w[i];
+                        V zi = ni + vb * v.z[i];
+                        V qi = wi + vb * v.q[i];
+                        V pi = di * ri + vb * v.p[i];
+                        V si = v.s[i] + va * pi;
+                        ri = ri - va * qi;
+                        wi = wi - va * zi;
+                        v.z[i] = zi;
+                        v.q[i] = qi;
+                        v.p[i] = pi;
+                        v.s[i] = si;
+                        v.r[i] = ri;
+                        v.w[i] = wi;
+                        mn[i] = di * wi;
+                        V ui = di * ri;
+                        a4[0] += ri * ui;
+                        a4[1] += wi * ui;
+                        a4[2] += ri * ri;
+                        if (count_cross) {
+                            V xs = v.x[i] + si;
+                            a4[3] += (xs < B.l(i) || xs > B.h(i)) ? one : zero;
+                        }
+                    });
+                    double o[5];
+                    if (!team_sum_scalar(T, a4, o, [&](const double (&d)[4], double (&r)[5]) {
+                            cg_scalar_step(d, r, alpha, beta, gamma, maxdec, C.eta2, ftol2, count_cross);
+                        }))
+                        return ST_TIMEOUT;
+                    ++st.spmv;
+                    ++st.cg;
+                    st.vec += count_cross ? 15 : 14;
+                    st.fl += 21;
+                    maxdec = o[4];
+                    if (flag_set(o[0]) || st.spmv >= C.max_spmv) break;
+                    alpha = o[1];
+                    beta = o[2];
+                    gamma = o[3];
+                    V *t = mc;
+                    mc = mn;
+                    mn = t;
                 }
             } else {
                 // textbook preconditioned CG

@@ -1,0 +1,203 @@
+// The persistent solve kernel of one system: one cooperative launch runs a
+// whole QP solve (steady), a whole backward-Euler run (transient: one
+// warm-started QP per step, Sec. 2.2.2 and Algorithm 1), or a mixed-precision
+// refinement loop (steady or per step), with no host round trip between
+// iterations.  The kernel is a template over (format, mode, CG variant); each
+// mode's instantiations are compiled in a translation unit of their own
+// (solve_grid_*.cu), which also returns them by (format, variant).
+#pragma once
+#include <stdint.h>
+#include "internal.h"
+#include "gpcg.cuh"
+#include "refine.cuh"
+
+namespace nnqp {
+
+constexpr int kSolveThreads = 256;
+constexpr int kCounters = 14;   // per-step int64 counters written by the kernel
+constexpr int kScalars = 4;     // per-step double results
+
+enum { MODE_STEADY = 0, MODE_TRANSIENT = 1, MODE_MIXED = 2, MODE_MIXED_TR = 3 };
+__host__ __device__ constexpr bool mode_transient(int m) { return m == MODE_TRANSIENT || m == MODE_MIXED_TR; }
+__host__ __device__ constexpr bool mode_mixed(int m) { return m == MODE_MIXED || m == MODE_MIXED_TR; }
+// Blocks per SM the kernel is compiled for: the transient drivers run one
+// block per SM on mid-size systems and get the larger register budget.
+__host__ __device__ constexpr int mode_min_blocks(int m) { return mode_transient(m) ? 2 : 3; }
+
+struct GridArgs {
+    int mode;
+    int64_t n, N, nslices;
+    SellF64 A;
+    CsrF64 Acsr;
+    SellF32Diff A32;
+    SellF64 M;
+    double lo, hi, inv_dt;
+    const double *b0;
+    const double *dinv64;
+    const float *dinv32;
+    const int32_t *free_node;
+    const double *c_in;     // full node vector (warm start)
+    double *c_out;          // full node vector (result), free entries written
+    double *c_hist;         // [nsteps][N] or null
+    int nsteps;
+    double *v64[11];        // x g p q r z s w gw b m2
+    float *v32[13];         // d g p q r z s w gw r32 l32 h32 m2
+    GpcgCtl ctl;
+    double rtol, den_fallback, b0norm, inner_rtol;
+    int max_ref;
+    GridBarrier *bar;
+    double *partials;
+    unsigned long long timeout_ns;
+    int bar_extra;          // arrivals the barrier waits for beyond the grid (0; 1 only in the stall test)
+    int64_t *counters;      // [nsteps][kCounters]
+    double *scalars;        // [nsteps][kScalars]
+    // projected L-BFGS
+    double *S, *Y;          // (m+1) slots of n doubles each
+    int m;
+    double h0;
+    // transient: initial iterate of step n+1 is P(2 c^(n) - c^(n-1)) when set
+    int predict;
+    double *xprev;          // [n] c^(n-1) at the free nodes
+    uint8_t *fmask;         // [n] face mask of the CG phases
+};
+
+// Initial iterate of a backward-Euler step: linear extrapolation of the last
+// two states, projected onto the box (the QP itself is unchanged; only the
+// starting point of its iteration moves).
+template <class Team>
+__device__ void transient_predict(const Rows &R, const GridArgs &a, double *x, int step) {
+    if (!a.predict) return;
+    R.each([&](int64_t i) {
+        const double xn = x[i];
+        if (step > 0) x[i] = clampv(xn + (xn - a.xprev[i]), a.lo, a.hi);
+        a.xprev[i] = xn;
+    });
+}
+
+// b of one backward-Euler step: b0 + M x / dt (Sec. 2.2.2, with c^(n));
+// returns ||b||_2 through den.
+template <class Team>
+__device__ bool transient_rhs(Team &T, const Rows &R, const GridArgs &a, const double *x, double *&b, double &den) {
+    double *bt = a.v64[9];
+    double acc[1] = {0.0};
+    a.M.apply(R, x, [&](int64_t i, double mx) {
+        const double bi = a.b0[i] + mx * a.inv_dt;
+        bt[i] = bi;
+        acc[0] += bi * bi;
+    });
+    if (!T.reduce(acc)) return false;
+    den = sqrt(acc[0]);
+    b = bt;
+    return true;
+}
+
+// Scatter of the step result to the full-node outputs and the per-step record.
+template <class Team>
+__device__ bool step_outputs(Team &T, const Rows &R, const GridArgs &a, const double *x, int step, int nsteps,
+                             int status, int64_t (&cnt)[kCounters], double gp2, double den) {
+    double acc[2] = {0.0, 0.0};
+    double *hist = a.c_hist ? a.c_hist + (int64_t)step * a.N : nullptr;
+    R.each([&](int64_t i) {
+        const double xi = x[i];
+        const int32_t v = a.free_node[i];
+        if (hist) hist[v] = xi;
+        if (step == nsteps - 1) a.c_out[v] = xi;
+        acc[0] += xi <= a.lo ? 1.0 : 0.0;
+        acc[1] += xi >= a.hi ? 1.0 : 0.0;
+    });
+    if (!T.reduce(acc)) return false;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        cnt[0] = status;
+        cnt[8] = (int64_t)acc[0];
+        cnt[9] = (int64_t)acc[1];
+        for (int k = 0; k < kCounters; ++k) a.counters[(int64_t)step * kCounters + k] = cnt[k];
+        a.scalars[step * kScalars + 0] = gp2;
+        a.scalars[step * kScalars + 1] = den;
+    }
+    return true;
+}
+
+// One instantiation per (format, mode) so that each kernel carries only the
+// code of its own path (register allocation is per kernel).
+template <int FMT, int MODE, int CGV>
+__global__ void __launch_bounds__(kSolveThreads, mode_min_blocks(MODE)) k_solve_grid(GridArgs a) {
+    __shared__ RedSmem sm;
+    GridTeam T{a.bar, a.partials, (int)gridDim.x + a.bar_extra, a.timeout_ns, 0, 0, &sm};
+    const Rows R = rows_of_block(a.n, a.nslices, blockIdx.x, gridDim.x);
+    double *x = a.v64[0];
+    R.each([&](int64_t i) { x[i] = a.c_in[a.free_node[i]]; });
+    if (!T.sync()) return;
+    const int nsteps = mode_transient(MODE) ? a.nsteps : 1;
+    for (int step = 0; step < nsteps; ++step) {
+        int status = ST_OK;
+        int64_t cnt[kCounters] = {0};
+        double den = a.b0norm, gp2 = 0.0;
+        double *b = const_cast<double *>(a.b0);
+        if (mode_transient(MODE)) {
+            if (!transient_rhs(T, R, a, x, b, den)) return;
+            cnt[1] += 1;   // products with M (FP64)
+            cnt[12] += 4;
+            transient_predict<GridTeam>(R, a, x, step);   // own rows; the solve's first pass syncs
+        }
+        if (!(den > 0.0)) den = a.den_fallback;
+        if (mode_mixed(MODE)) {
+            GpcgVecs<float> v{a.v32[0], a.v32[1], a.v32[2], a.v32[3], a.v32[4], a.v32[5],
+                              a.v32[6], a.v32[7], a.v32[8], a.v32[9], a.dinv32, a.fmask, a.v32[12]};
+            GpcgVecs<double> v64{x, a.v64[1], a.v64[2], a.v64[3], a.v64[4], a.v64[5],
+                                 a.v64[6], a.v64[7], a.v64[8], b, a.dinv64, a.fmask, a.v64[10]};
+            MixedStats ms;
+            status = mixed_solve<CGV, true>(T, R, a.A, a.A32, a.lo, a.hi, b, x, v, a.v32[9], a.v32[10], a.v32[11], v64,
+                                 a.rtol * den, a.inner_rtol, a.max_ref, a.ctl.max_spmv,
+                                 inner_product_cap(a.n), a.ctl, a.ctl, ms);
+            if (status == ST_TIMEOUT) return;
+            cnt[1] += ms.spmv64;
+            cnt[2] += ms.spmv32;
+            cnt[3] = ms.cg;
+            cnt[4] = ms.phases;
+            cnt[5] = ms.refinements;
+            cnt[6] = ms.vec64;
+            cnt[7] = ms.vec32;
+            cnt[11] = ms.fallback;
+            cnt[12] += ms.fl64;
+            cnt[13] += ms.fl32;
+            gp2 = ms.gp2;
+        } else {
+            GpcgVecs<double> v{x, a.v64[1], a.v64[2], a.v64[3], a.v64[4], a.v64[5],
+                               a.v64[6], a.v64[7], a.v64[8], b, a.dinv64, a.fmask, a.v64[10]};
+            GpcgCtl c = a.ctl;
+            c.tol = a.rtol * den;
+            c.face_tol = 0.5 * c.tol;
+            GpcgStats gs;
+            if (FMT == 0)
+                status = gpcg_solve<GridTeam, SellF64, double, CGV>(T, R, a.A, Bounds<double>{a.lo, a.hi, nullptr, nullptr}, v, c, gs);
+            else
+                status = gpcg_solve<GridTeam, CsrF64, double, CGV>(T, R, a.Acsr, Bounds<double>{a.lo, a.hi, nullptr, nullptr}, v, c, gs);
+            if (status == ST_TIMEOUT) return;
+            x = v.x;
+            // keep the solution in slot 0 so that the next step starts there
+            if (x != a.v64[0]) {
+                R.each([&](int64_t i) { a.v64[0][i] = x[i]; });
+                x = a.v64[0];
+                if (!T.sync()) return;
+            }
+            cnt[1] += gs.spmv;
+            cnt[3] = gs.cg;
+            cnt[4] = gs.phases;
+            cnt[6] = gs.vec;
+            cnt[12] += gs.fl;
+            gp2 = gs.gp2;
+        }
+        if (!step_outputs(T, R, a, x, step, nsteps, status, cnt, gp2, den)) return;
+    }
+}
+
+using GridKernel = void (*)(GridArgs);
+
+// Kernel of one mode for format fmt (NN_FMT_SELL / NN_FMT_CSR) and CG
+// variant cgv (0, 1, 2); nullptr if that combination is not built.
+GridKernel grid_kernel_steady(int fmt, int cgv);
+GridKernel grid_kernel_transient(int fmt, int cgv);
+GridKernel grid_kernel_mixed(int fmt, int cgv);
+GridKernel grid_kernel_mixed_transient(int fmt, int cgv);
+
+}  // namespace nnqp

@@ -6,16 +6,16 @@
 // built from the last m pairs (s, y) = (x+ - x, g+ - g), d is zeroed on the
 // binding set, and x+ = P(x + alpha d) with alpha halved until the Armijo
 // condition holds.  Pairs with s'y <= 1e-12 |s||y| are skipped.  H is
-// applied in the compact form (lbfgs_small.h), so one iteration is a fixed
-// number of fused passes: dots S'gP, Y'gP -> direction -> trial point ->
-// product A w fused with the new pair and all dots the model update needs.
+// applied in the compact form (lbfgs_small.h), so one iteration is two fused
+// passes: direction + trial point -> product A w fused with the new pair and
+// all dots that the model update and the next direction need.
 #pragma once
 #include "gpcg.cuh"
 #include "lbfgs_small.h"
 
 namespace nnqp {
 
-constexpr int kLbMaxM = 6;   // pairs kept on the device (reductions are 3m+6 wide)
+constexpr int kLbMaxM = 6;   // pairs kept on the device (reductions are 5m+9 wide)
 
 struct LbSmem {
     double SY[kLbfgsMax * kLbfgsMax];
@@ -37,7 +37,29 @@ struct LbStats {
     double gp2 = 0.0;
 };
 
+// Layout of the per-trial reduction (one per product).
+constexpr int kLbW = 9 + 5 * kLbMaxM;
+static_assert(kLbW <= kMaxRed, "L-BFGS reduction wider than the team reduction buffers");
+enum : int {
+    LB_GDX = 0,   // g'(w - x)                   (trial pass)
+    LB_QD = 1,    // (g + gw)'s = 2 (q(w) - q(x))
+    LB_GP2 = 2,   // ||gP(w)||^2
+    LB_SY = 3,    // s'y
+    LB_SS = 4,    // s's
+    LB_YY = 5,    // y'y
+    LB_GD = 6,    // gP(x)'d                     (trial pass, first trial)
+    LB_SNG = 7,   // s'gP(w)
+    LB_YNG = 8,   // y'gP(w)
+    LB_X = 9,     // [j]: s'y_j, y_j's... : s y_j | s_j y | y y_j | s_j gP(w) | y_j gP(w)
+};
+
 // S, Y: (m+1) slots of n doubles each (one spare slot receives the trial pair).
+// One iteration = (trial pass: direction on the first trial, trial point)
+// -> barrier -> (product A w fused with the trial pair and every dot that the
+// Armijo test, the pair update and the NEXT iteration's model need) ->
+// reduction.  The model coefficients of the next iteration therefore come
+// from the accepted trial's reduction, so an accepted first trial costs one
+// barrier and one reduction per product.
 template <class Team, class Op>
 __device__ int lbfgs_solve(Team &T, const Rows &R, const Op &A, double lo, double hi, const double *b, double *&x,
                            double *&g, double *d, double *&w, double *&gw, double *S, double *Y, int64_t n,
@@ -45,6 +67,7 @@ __device__ int lbfgs_solve(Team &T, const Rows &R, const Op &A, double lo, doubl
     const int m = C.m;
     int ord[kLbMaxM];
     int k = 0, spare = 0;
+    double uv[2 * kLbMaxM];   // S_j'gP(x), Y_j'gP(x) for the pairs in ord
     R.each([&](int64_t i) { x[i] = clampv(x[i], lo, hi); });
     st.vec += 2;
     if (!T.sync()) return ST_TIMEOUT;
@@ -67,68 +90,48 @@ __device__ int lbfgs_solve(Team &T, const Rows &R, const Op &A, double lo, doubl
         if (st.gp2 <= tol2) return ST_OK;
         if (st.spmv >= C.max_spmv) return ST_NOT_CONVERGED;
         ++st.iters;
-        // ---- model coefficients from u = S'gP, v = Y'gP
+        // ---- model coefficients from u = S'gP, v = Y'gP (carried over)
         bool use_model = k > 0;
         if (use_model) {
-            double a[2 * kLbMaxM] = {0.0};
-            R.each([&](int64_t i) {
-                const double gp = proj_grad(x[i], g[i], lo, hi);
-#pragma unroll
-                for (int j = 0; j < kLbMaxM; ++j)
-                    if (j < k) {
-                        a[j] += S[(int64_t)ord[j] * n + i] * gp;
-                        a[kLbMaxM + j] += Y[(int64_t)ord[j] * n + i] * gp;
-                    }
-            });
-            if (!T.reduce(a)) return ST_TIMEOUT;
-            st.vec += 2 + 2 * k;
             if (threadIdx.x == 0) {
                 const double gamma = sm.SY[(k - 1) * kLbfgsMax + (k - 1)] / sm.YY[(k - 1) * kLbfgsMax + (k - 1)];
-                sm.ok = lbfgs_coefficients(k, sm.SY, sm.YY, a, a + kLbMaxM, gamma, sm.cs, sm.cy) ? 1 : 0;
+                sm.ok = lbfgs_coefficients(k, sm.SY, sm.YY, uv, uv + kLbMaxM, gamma, sm.cs, sm.cy) ? 1 : 0;
                 sm.cs[kLbfgsMax - 1] = gamma;
             }
             __syncthreads();
             use_model = sm.ok != 0;
         }
-        // ---- direction d = -H gP, zero on the binding set; descent test
-        double gd;
-        for (int attempt = 0; attempt < 2; ++attempt) {
-            const double gamma = use_model ? sm.cs[kLbfgsMax - 1] : C.h0;
-            double a[1] = {0.0};
-            R.each([&](int64_t i) {
-                const double xi = x[i], gp = proj_grad(xi, g[i], lo, hi);
-                double hg = gamma * gp;
-                if (use_model) {
-#pragma unroll
-                    for (int j = 0; j < kLbMaxM; ++j)
-                        if (j < k) hg += sm.cs[j] * S[(int64_t)ord[j] * n + i] + sm.cy[j] * Y[(int64_t)ord[j] * n + i];
-                }
-                const bool binding = (xi <= lo || xi >= hi) && gp == 0.0;
-                const double di = binding ? 0.0 : -hg;
-                d[i] = di;
-                a[0] += gp * di;
-            });
-            if (!T.reduce(a)) return ST_TIMEOUT;
-            st.vec += use_model ? 3 + 2 * k : 3;
-            gd = a[0];
-            if (gd < 0.0 || !use_model) break;
-            use_model = false;   // not a descent direction: drop the memory
-            k = 0;
-            ++st.resets;
-        }
-        if (!(gd < 0.0)) return ST_NUMERIC;
-        // ---- projected backtracking search
+        // ---- projected backtracking search along d = -H gP (zero on the binding set)
         double alpha = 1.0;
-        bool accepted = false;
-        double a[3 * kLbMaxM + 6];
+        bool accepted = false, have_d = false;
+        double a[kLbW];
         for (int ls = 0; ls < 60; ++ls) {
-            for (int q = 0; q < 3 * kLbMaxM + 6; ++q) a[q] = 0.0;
+#pragma unroll
+            for (int q = 0; q < kLbW; ++q) a[q] = 0.0;
+            const double gamma = use_model ? sm.cs[kLbfgsMax - 1] : C.h0;
+            const int kk = use_model ? k : 0;
+            const bool first = !have_d;
             R.each([&](int64_t i) {
                 const double xi = x[i];
-                const double wi = clampv(xi + alpha * d[i], lo, hi);
+                double di;
+                if (first) {
+                    const double gp = proj_grad(xi, g[i], lo, hi);
+                    double hg = gamma * gp;
+#pragma unroll
+                    for (int j = 0; j < kLbMaxM; ++j)
+                        if (j < kk) hg += sm.cs[j] * S[(int64_t)ord[j] * n + i] + sm.cy[j] * Y[(int64_t)ord[j] * n + i];
+                    const bool binding = (xi <= lo || xi >= hi) && gp == 0.0;
+                    di = binding ? 0.0 : -hg;
+                    d[i] = di;
+                    a[LB_GD] += gp * di;
+                } else {
+                    di = d[i];
+                }
+                const double wi = clampv(xi + alpha * di, lo, hi);
                 w[i] = wi;
-                a[0] += g[i] * (wi - xi);
+                a[LB_GDX] += g[i] * (wi - xi);
             });
+            st.vec += first ? 4 + 2 * kk : 4;
             if (!T.sync()) return ST_TIMEOUT;
             double *Sn = S + (int64_t)spare * n, *Yn = Y + (int64_t)spare * n;
             A.apply(R, w, [&](int64_t i, double aw) {
@@ -138,25 +141,40 @@ __device__ int lbfgs_solve(Team &T, const Rows &R, const Op &A, double lo, doubl
                 const double si = wi - x[i], yi = gwi - g[i];
                 Sn[i] = si;
                 Yn[i] = yi;
-                a[1] += (g[i] + gwi) * si;
+                a[LB_QD] += (g[i] + gwi) * si;
                 const double gp = proj_grad(wi, gwi, lo, hi);
-                a[2] += gp * gp;
-                a[3] += si * yi;
-                a[4] += si * si;
-                a[5] += yi * yi;
+                a[LB_GP2] += gp * gp;
+                a[LB_SY] += si * yi;
+                a[LB_SS] += si * si;
+                a[LB_YY] += yi * yi;
+                a[LB_SNG] += si * gp;
+                a[LB_YNG] += yi * gp;
 #pragma unroll
                 for (int j = 0; j < kLbMaxM; ++j)
                     if (j < k) {
                         const double sj = S[(int64_t)ord[j] * n + i], yj = Y[(int64_t)ord[j] * n + i];
-                        a[6 + j] += si * yj;
-                        a[6 + kLbMaxM + j] += sj * yi;
-                        a[6 + 2 * kLbMaxM + j] += yi * yj;
+                        a[LB_X + j] += si * yj;
+                        a[LB_X + kLbMaxM + j] += sj * yi;
+                        a[LB_X + 2 * kLbMaxM + j] += yi * yj;
+                        a[LB_X + 3 * kLbMaxM + j] += sj * gp;
+                        a[LB_X + 4 * kLbMaxM + j] += yj * gp;
                     }
             });
             if (!T.reduce(a)) return ST_TIMEOUT;
             ++st.spmv;
             st.vec += 6 + 2 * k + 3;
-            if (0.5 * a[1] <= C.mu * a[0]) {
+            if (first) {
+                have_d = true;
+                if (!(a[LB_GD] < 0.0)) {
+                    if (!use_model) return ST_NUMERIC;
+                    use_model = false;   // not a descent direction: drop the memory
+                    k = 0;
+                    have_d = false;
+                    ++st.resets;
+                    continue;
+                }
+            }
+            if (0.5 * a[LB_QD] <= C.mu * a[LB_GDX]) {
                 accepted = true;
                 break;
             }
@@ -166,11 +184,11 @@ __device__ int lbfgs_solve(Team &T, const Rows &R, const Op &A, double lo, doubl
         if (!accepted) return ST_NOT_CONVERGED;
         double *t = x; x = w; w = t;
         t = g; g = gw; gw = t;
-        st.gp2 = a[2];
-        // ---- memory update
-        if (a[3] > 1e-12 * sqrt(a[4] * a[5])) {
+        st.gp2 = a[LB_GP2];
+        // ---- memory update; uv follows the pairs to their new positions
+        if (a[LB_SY] > 1e-12 * sqrt(a[LB_SS] * a[LB_YY])) {
+            const int drop = k == m ? 1 : 0;
             if (threadIdx.x == 0) {
-                int drop = k == m ? 1 : 0;
                 // new dots indexed by the old positions j; after a drop old j maps to j - 1
                 if (drop)
                     for (int i = 0; i + 1 < k; ++i)
@@ -181,15 +199,24 @@ __device__ int lbfgs_solve(Team &T, const Rows &R, const Op &A, double lo, doubl
                 const int kn = k - drop;   // old pairs kept
                 for (int j = 0; j < kn; ++j) {
                     const int oj = j + drop;
-                    sm.SY[kn * kLbfgsMax + j] = a[6 + oj];
-                    sm.SY[j * kLbfgsMax + kn] = a[6 + kLbMaxM + oj];
-                    sm.YY[kn * kLbfgsMax + j] = sm.YY[j * kLbfgsMax + kn] = a[6 + 2 * kLbMaxM + oj];
+                    sm.SY[kn * kLbfgsMax + j] = a[LB_X + oj];
+                    sm.SY[j * kLbfgsMax + kn] = a[LB_X + kLbMaxM + oj];
+                    sm.YY[kn * kLbfgsMax + j] = sm.YY[j * kLbfgsMax + kn] = a[LB_X + 2 * kLbMaxM + oj];
                 }
-                sm.SY[kn * kLbfgsMax + kn] = a[3];
-                sm.YY[kn * kLbfgsMax + kn] = a[5];
+                sm.SY[kn * kLbfgsMax + kn] = a[LB_SY];
+                sm.YY[kn * kLbfgsMax + kn] = a[LB_YY];
             }
             __syncthreads();
-            if (k == m) {
+            const int kn = k - drop;
+#pragma unroll
+            for (int j = 0; j < kLbMaxM; ++j)
+                if (j < kn) {
+                    uv[j] = a[LB_X + 3 * kLbMaxM + j + drop];
+                    uv[kLbMaxM + j] = a[LB_X + 4 * kLbMaxM + j + drop];
+                }
+            uv[kn] = a[LB_SNG];
+            uv[kLbMaxM + kn] = a[LB_YNG];
+            if (drop) {
                 const int old = ord[0];
                 for (int j = 0; j + 1 < k; ++j) ord[j] = ord[j + 1];
                 ord[k - 1] = spare;
@@ -207,6 +234,13 @@ __device__ int lbfgs_solve(Team &T, const Rows &R, const Op &A, double lo, doubl
                     }
                 }
             }
+        } else {
+#pragma unroll
+            for (int j = 0; j < kLbMaxM; ++j)
+                if (j < k) {
+                    uv[j] = a[LB_X + 3 * kLbMaxM + j];
+                    uv[kLbMaxM + j] = a[LB_X + 4 * kLbMaxM + j];
+                }
         }
     }
 }

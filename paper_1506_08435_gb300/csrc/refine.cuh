@@ -31,7 +31,27 @@ struct MixedStats {
     double gp2 = 0.0;
 };
 
-template <int CGV, class Team, class Op64, class Op32>
+// With SPLIT the inner and fallback solves are separate (non-inlined) calls:
+// the registers that the refinement loop keeps live across them are saved
+// once per call instead of competing with the solver's inner loops for
+// registers (the grid kernels, compiled for 80 or 128 registers).  Without
+// SPLIT they are inlined (the batch kernels, which have 255 registers).
+template <class Team, class Op, typename V, int CGV>
+__device__ __noinline__ int gpcg_call_split(Team &T, const Rows &R, const Op &A, const Bounds<V> &B,
+                                            GpcgVecs<V> &v, const GpcgCtl &C, GpcgStats &st) {
+    return gpcg_solve<Team, Op, V, CGV>(T, R, A, B, v, C, st);
+}
+
+template <bool SPLIT, class Team, class Op, typename V, int CGV>
+__device__ __forceinline__ int gpcg_call(Team &T, const Rows &R, const Op &A, const Bounds<V> &B, GpcgVecs<V> &v,
+                                         const GpcgCtl &C, GpcgStats &st) {
+    if constexpr (SPLIT)
+        return gpcg_call_split<Team, Op, V, CGV>(T, R, A, B, v, C, st);
+    else
+        return gpcg_solve<Team, Op, V, CGV>(T, R, A, B, v, C, st);
+}
+
+template <int CGV, bool SPLIT, class Team, class Op64, class Op32>
 __device__ int mixed_solve(Team &T, const Rows &R, const Op64 &A, const Op32 &A32, double lo, double hi,
                            const double *b, double *x, GpcgVecs<float> &v, float *r32, float *l32, float *h32,
                            GpcgVecs<double> &v64, double tol, double inner_rtol, int max_ref, int64_t max_spmv,
@@ -70,7 +90,7 @@ __device__ int mixed_solve(Team &T, const Rows &R, const Op64 &A, const Op32 &A3
             c.max_spmv = max_spmv - st.spmv64 - st.spmv32;
             GpcgStats gs;
             v64.x = x;
-            const int s = gpcg_solve<Team, Op64, double, CGV>(T, R, A, Bounds<double>{lo, hi, nullptr, nullptr}, v64, c, gs);
+            const int s = gpcg_call<SPLIT, Team, Op64, double, CGV>(T, R, A, Bounds<double>{lo, hi, nullptr, nullptr}, v64, c, gs);
             st.spmv64 += gs.spmv;
             st.cg += gs.cg;
             st.phases += gs.phases;
@@ -97,7 +117,7 @@ __device__ int mixed_solve(Team &T, const Rows &R, const Op64 &A, const Op32 &A3
         if (c.max_spmv > inner_cap) c.max_spmv = inner_cap;
         GpcgStats is;
         Bounds<float> B{0.0, 0.0, l32, h32};
-        int s = gpcg_solve<Team, Op32, float, CGV>(T, R, A32, B, v, c, is);
+        int s = gpcg_call<SPLIT, Team, Op32, float, CGV>(T, R, A32, B, v, c, is);
         st.spmv32 += is.spmv;
         st.cg += is.cg;
         st.phases += is.phases;

@@ -1,191 +1,16 @@
-// Persistent single-system solves: one cooperative launch runs a whole QP
-// solve (steady), a whole backward-Euler run (transient: one warm-started QP
-// per step, Sec. 2.2.2 and Algorithm 1), or a mixed-precision refinement
-// loop, with no host round trip between iterations.
+// Single-system solves, host side: scratch, grid sizing and the cooperative
+// launch of the persistent solve kernels (grid.cuh), the projected L-BFGS
+// driver kernel, the FP64 KKT measure and the stand-alone products.
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
 #include <algorithm>
 #include <mutex>
 #include "internal.h"
-#include "gpcg.cuh"
-#include "refine.cuh"
+#include "grid.cuh"
 #include "lbfgs.cuh"
 
 namespace nnqp {
-
-constexpr int kSolveThreads = 256;
-constexpr int kCounters = 14;   // per-step int64 counters written by the kernel
-constexpr int kScalars = 4;     // per-step double results
-
-enum { MODE_STEADY = 0, MODE_TRANSIENT = 1, MODE_MIXED = 2 };
-
-struct GridArgs {
-    int mode;
-    int64_t n, N, nslices;
-    SellF64 A;
-    CsrF64 Acsr;
-    SellF32Diff A32;
-    SellF64 M;
-    double lo, hi, inv_dt;
-    const double *b0;
-    const double *dinv64;
-    const float *dinv32;
-    const int32_t *free_node;
-    const double *c_in;     // full node vector (warm start)
-    double *c_out;          // full node vector (result), free entries written
-    double *c_hist;         // [nsteps][N] or null
-    int nsteps;
-    double *v64[10];        // x g p q r z s w gw b
-    float *v32[12];         // d g p q r z s w gw r32 l32 h32
-    GpcgCtl ctl;
-    double rtol, den_fallback, b0norm, inner_rtol;
-    int max_ref;
-    GridBarrier *bar;
-    double *partials;
-    unsigned long long timeout_ns;
-    int bar_extra;          // arrivals the barrier waits for beyond the grid (0; 1 only in the stall test)
-    int64_t *counters;      // [nsteps][kCounters]
-    double *scalars;        // [nsteps][kScalars]
-    // projected L-BFGS
-    double *S, *Y;          // (m+1) slots of n doubles each
-    int m;
-    double h0;
-    // transient: initial iterate of step n+1 is P(2 c^(n) - c^(n-1)) when set
-    int predict;
-    double *xprev;          // [n] c^(n-1) at the free nodes
-    uint8_t *fmask;         // [n] face mask of the CG phases
-};
-
-// Initial iterate of a backward-Euler step: linear extrapolation of the last
-// two states, projected onto the box (the QP itself is unchanged; only the
-// starting point of its iteration moves).
-template <class Team>
-__device__ void transient_predict(const Rows &R, const GridArgs &a, double *x, int step) {
-    if (!a.predict) return;
-    R.each([&](int64_t i) {
-        const double xn = x[i];
-        if (step > 0) x[i] = clampv(xn + (xn - a.xprev[i]), a.lo, a.hi);
-        a.xprev[i] = xn;
-    });
-}
-
-// b of one backward-Euler step: b0 + M x / dt (Sec. 2.2.2, with c^(n));
-// returns ||b||_2 through den.
-template <class Team>
-__device__ bool transient_rhs(Team &T, const Rows &R, const GridArgs &a, const double *x, double *&b, double &den) {
-    double *bt = a.v64[9];
-    double acc[1] = {0.0};
-    a.M.apply(R, x, [&](int64_t i, double mx) {
-        const double bi = a.b0[i] + mx * a.inv_dt;
-        bt[i] = bi;
-        acc[0] += bi * bi;
-    });
-    if (!T.reduce(acc)) return false;
-    den = sqrt(acc[0]);
-    b = bt;
-    return true;
-}
-
-// Scatter of the step result to the full-node outputs and the per-step record.
-template <class Team>
-__device__ bool step_outputs(Team &T, const Rows &R, const GridArgs &a, const double *x, int step, int nsteps,
-                             int status, int64_t (&cnt)[kCounters], double gp2, double den) {
-    double acc[2] = {0.0, 0.0};
-    double *hist = a.c_hist ? a.c_hist + (int64_t)step * a.N : nullptr;
-    R.each([&](int64_t i) {
-        const double xi = x[i];
-        const int32_t v = a.free_node[i];
-        if (hist) hist[v] = xi;
-        if (step == nsteps - 1) a.c_out[v] = xi;
-        acc[0] += xi <= a.lo ? 1.0 : 0.0;
-        acc[1] += xi >= a.hi ? 1.0 : 0.0;
-    });
-    if (!T.reduce(acc)) return false;
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        cnt[0] = status;
-        cnt[8] = (int64_t)acc[0];
-        cnt[9] = (int64_t)acc[1];
-        for (int k = 0; k < kCounters; ++k) a.counters[(int64_t)step * kCounters + k] = cnt[k];
-        a.scalars[step * kScalars + 0] = gp2;
-        a.scalars[step * kScalars + 1] = den;
-    }
-    return true;
-}
-
-// One instantiation per (format, mode) so that each kernel carries only the
-// code of its own path (register allocation is per kernel).
-template <int FMT, int MODE, int CGV>
-__global__ void __launch_bounds__(kSolveThreads, 3) k_solve_grid(GridArgs a) {
-    __shared__ RedSmem sm;
-    GridTeam T{a.bar, a.partials, (int)gridDim.x + a.bar_extra, a.timeout_ns, 0, 0, &sm};
-    const Rows R = rows_of_block(a.n, a.nslices, blockIdx.x, gridDim.x);
-    double *x = a.v64[0];
-    R.each([&](int64_t i) { x[i] = a.c_in[a.free_node[i]]; });
-    if (!T.sync()) return;
-    const int nsteps = MODE == MODE_TRANSIENT ? a.nsteps : 1;
-    for (int step = 0; step < nsteps; ++step) {
-        int status = ST_OK;
-        int64_t cnt[kCounters] = {0};
-        double den = a.b0norm, gp2 = 0.0;
-        double *b = const_cast<double *>(a.b0);
-        if (MODE == MODE_TRANSIENT) {
-            if (!transient_rhs(T, R, a, x, b, den)) return;
-            cnt[1] += 1;   // products with M (FP64)
-            cnt[12] += 4;
-            transient_predict<GridTeam>(R, a, x, step);   // own rows; the solve's first pass syncs
-        }
-        if (!(den > 0.0)) den = a.den_fallback;
-        if (MODE == MODE_MIXED) {
-            GpcgVecs<float> v{a.v32[0], a.v32[1], a.v32[2], a.v32[3], a.v32[4], a.v32[5],
-                              a.v32[6], a.v32[7], a.v32[8], a.v32[9], a.dinv32, a.fmask};
-            GpcgVecs<double> v64{x, a.v64[1], a.v64[2], a.v64[3], a.v64[4], a.v64[5],
-                                 a.v64[6], a.v64[7], a.v64[8], b, a.dinv64, a.fmask};
-            MixedStats ms;
-            status = mixed_solve<CGV>(T, R, a.A, a.A32, a.lo, a.hi, b, x, v, a.v32[9], a.v32[10], a.v32[11], v64,
-                                 a.rtol * den, a.inner_rtol, a.max_ref, a.ctl.max_spmv,
-                                 inner_product_cap(a.n), a.ctl, a.ctl, ms);
-            if (status == ST_TIMEOUT) return;
-            cnt[1] += ms.spmv64;
-            cnt[2] += ms.spmv32;
-            cnt[3] = ms.cg;
-            cnt[4] = ms.phases;
-            cnt[5] = ms.refinements;
-            cnt[6] = ms.vec64;
-            cnt[7] = ms.vec32;
-            cnt[11] = ms.fallback;
-            cnt[12] += ms.fl64;
-            cnt[13] += ms.fl32;
-            gp2 = ms.gp2;
-        } else {
-            GpcgVecs<double> v{x, a.v64[1], a.v64[2], a.v64[3], a.v64[4], a.v64[5],
-                               a.v64[6], a.v64[7], a.v64[8], b, a.dinv64, a.fmask};
-            GpcgCtl c = a.ctl;
-            c.tol = a.rtol * den;
-            c.face_tol = 0.5 * c.tol;
-            GpcgStats gs;
-            if (FMT == 0)
-                status = gpcg_solve<GridTeam, SellF64, double, CGV>(T, R, a.A, Bounds<double>{a.lo, a.hi, nullptr, nullptr}, v, c, gs);
-            else
-                status = gpcg_solve<GridTeam, CsrF64, double, CGV>(T, R, a.Acsr, Bounds<double>{a.lo, a.hi, nullptr, nullptr}, v, c, gs);
-            if (status == ST_TIMEOUT) return;
-            x = v.x;
-            // keep the solution in slot 0 so that the next step starts there
-            if (x != a.v64[0]) {
-                R.each([&](int64_t i) { a.v64[0][i] = x[i]; });
-                x = a.v64[0];
-                if (!T.sync()) return;
-            }
-            cnt[1] += gs.spmv;
-            cnt[3] = gs.cg;
-            cnt[4] = gs.phases;
-            cnt[6] = gs.vec;
-            cnt[12] += gs.fl;
-            gp2 = gs.gp2;
-        }
-        if (!step_outputs(T, R, a, x, step, nsteps, status, cnt, gp2, den)) return;
-    }
-}
 
 // The same driver with the projected L-BFGS solver (FP64, SELL).
 __global__ void __launch_bounds__(kSolveThreads) k_lbfgs_grid(GridArgs a) {
@@ -345,6 +170,15 @@ int max_coresident(K kern) {
     return std::max(per, 1) * device_sms();
 }
 
+GridKernel grid_kernel(int mode, int fmt, int cgv) {
+    switch (mode) {
+        case MODE_TRANSIENT: return grid_kernel_transient(fmt, cgv);
+        case MODE_MIXED: return grid_kernel_mixed(fmt, cgv);
+        case MODE_MIXED_TR: return grid_kernel_mixed_transient(fmt, cgv);
+        default: return grid_kernel_steady(fmt, cgv);
+    }
+}
+
 // algorithmic bytes of one product (paper's MatMult model, Sec. 4):
 // nnz (s_v + 4) + 4 (n + 1) + s_x n (x read) + s_x n (y written)
 double bytes_spmv(int64_t nnz, int64_t n, int sv, int sx) {
@@ -384,17 +218,17 @@ void fill_info(const nn_system *s, const int64_t *cnt, const double *sc, int pre
 nn_status run_grid(nn_system *s, const nn_solve_opts *o, int mode, int nsteps, const double *c_in, double *c_out,
                    double *c_hist, cudaStream_t st, nn_solve_info *infos, int ninfos) {
     const int64_t n = s->NF, N = s->N;
-    const bool mixed = mode == MODE_MIXED;
+    const bool mixed = mode_mixed(mode);
     const int fmt = o->format;
     if (mixed && !s->has_mixed) {
         set_error("mixed precision needs a system assembled with build_mixed = 1");
         return NN_ERR_INVALID_ARG;
     }
-    if (mode == MODE_TRANSIENT && !(s->dt > 0.0)) {
+    if (mode_transient(mode) && !(s->dt > 0.0)) {
         set_error("transient solve on a steady system (dt = 0)");
         return NN_ERR_INVALID_ARG;
     }
-    if (mode != MODE_TRANSIENT && s->dt > 0.0) {
+    if (!mode_transient(mode) && s->dt > 0.0) {
         set_error("steady solve on a transient system: use nn_step or nn_transient");
         return NN_ERR_INVALID_ARG;
     }
@@ -425,10 +259,10 @@ nn_status run_grid(nn_system *s, const nn_solve_opts *o, int mode, int nsteps, c
     a.c_out = c_out;
     a.c_hist = c_hist;
     a.nsteps = nsteps;
-    for (int k = 0; k < 10; ++k) NN_TRY(S.a.alloc(&a.v64[k], n, st));
+    for (int k = 0; k < 11; ++k) NN_TRY(S.a.alloc(&a.v64[k], n, st));
     NN_TRY(S.a.alloc(&a.fmask, n, st));
     if (mixed)
-        for (int k = 0; k < 12; ++k) NN_TRY(S.a.alloc(&a.v32[k], n, st));
+        for (int k = 0; k < 13; ++k) NN_TRY(S.a.alloc(&a.v32[k], n, st));
     a.ctl.max_spmv = o->max_iter;
     a.ctl.gp_max = 50;
     a.ctl.cg_max = 1 << 30;
@@ -461,14 +295,12 @@ nn_status run_grid(nn_system *s, const nn_solve_opts *o, int mode, int nsteps, c
         NN_TRY(S.a.alloc(&a.Y, (size_t)(a.m + 1) * n, st));
     }
     a.predict = o->extrapolate;
-    if (mode == MODE_TRANSIENT && a.predict) NN_TRY(S.a.alloc(&a.xprev, n, st));
-    const bool cg2 = a.ctl.cg_variant == 1;
-    void (*kern)(GridArgs) =
-        lbfgs                    ? k_lbfgs_grid
-        : fmt == NN_FMT_CSR      ? (cg2 ? k_solve_grid<1, MODE_STEADY, 1> : k_solve_grid<1, MODE_STEADY, 0>)
-        : mode == MODE_MIXED     ? (cg2 ? k_solve_grid<0, MODE_MIXED, 1> : k_solve_grid<0, MODE_MIXED, 0>)
-        : mode == MODE_TRANSIENT ? (cg2 ? k_solve_grid<0, MODE_TRANSIENT, 1> : k_solve_grid<0, MODE_TRANSIENT, 0>)
-                                 : (cg2 ? k_solve_grid<0, MODE_STEADY, 1> : k_solve_grid<0, MODE_STEADY, 0>);
+    if (mode_transient(mode) && a.predict) NN_TRY(S.a.alloc(&a.xprev, n, st));
+    GridKernel kern = lbfgs ? k_lbfgs_grid : grid_kernel(mode, fmt, a.ctl.cg_variant);
+    if (!kern) {
+        set_error("CG variant %d is not available for this mode and format", a.ctl.cg_variant);
+        return NN_ERR_INVALID_ARG;
+    }
     const int maxg = max_coresident(kern);
     // one slice per warp at least; grids of up to one block per SM while that
     // covers the rows in a few slices per warp (fewer barrier arrivals), the
@@ -689,16 +521,17 @@ nn_status solve_entry(nn_system *s, const nn_solve_opts *o, int mode, int nsteps
 }
 
 int mode_for(const nn_system *s, const nn_solve_opts *o) {
-    if (s->dt > 0.0) return MODE_TRANSIENT;
+    if (s->dt > 0.0) return o->precision == NN_PREC_MIXED ? MODE_MIXED_TR : MODE_TRANSIENT;
     return o->precision == NN_PREC_MIXED ? MODE_MIXED : MODE_STEADY;
 }
 
 // Co-resident blocks of the steady/mixed solve kernel on the current device.
 int solve_grid_capacity() {
-    int c = max_coresident(k_solve_grid<0, MODE_STEADY, 0>);
-    c = std::min(c, max_coresident(k_solve_grid<0, MODE_STEADY, 1>));
-    c = std::min(c, max_coresident(k_solve_grid<0, MODE_MIXED, 0>));
-    return std::min(c, max_coresident(k_solve_grid<0, MODE_MIXED, 1>));
+    int c = 1 << 30;
+    for (int mode : {MODE_STEADY, MODE_MIXED})
+        for (int v = 0; v < 3; ++v)
+            if (GridKernel k = grid_kernel(mode, NN_FMT_SELL, v)) c = std::min(c, max_coresident(k));
+    return c;
 }
 
 // One steady solve with a fixed persistent grid (serving).

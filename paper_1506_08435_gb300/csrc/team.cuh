@@ -15,7 +15,7 @@
 
 namespace nnqp {
 
-constexpr int kMaxRed = 24;       // doubles per reduction call (at most)
+constexpr int kMaxRed = 40;       // doubles per reduction call (at most)
 constexpr int kMaxWarps = 32;
 
 struct GridBarrier {
@@ -56,29 +56,100 @@ __device__ __forceinline__ int ld_relaxed_i32(const int *p) {
 struct RedSmem {
     double warp[kMaxWarps][kMaxRed];
     double bcast[kMaxRed];
+    double sc[16];                // results of scalar steps done by warp 0
     int flag;
 };
 
-// Sum of v over the block; the result (taken from lane 0 of warp 0, so it
-// is one fixed summation order) is returned in v on every thread.
+// Warp stage of a block sum: K values per lane are summed over the warp's 32
+// lanes with a transposing butterfly.  While a lane holds more than one
+// value, each level sends half of them to the partner lane (offset o) and
+// keeps the other half, so every FP64 add is useful (K/2 + K/4 + ... adds
+// instead of 5 K).  On GB300 every FP64 warp instruction occupies the SM's
+// narrow FP64 pipe for many cycles whatever the active mask, so the count of
+// FP64 instructions, not their latency, is what a reduction costs.  P is K
+// rounded up to a power of two; on return lane l holds the warp totals of
+// indices ((l >> (5 - LT)) * CF + j), j < CF, with LT the number of
+// transposing levels and CF = P >> LT values left per lane.  The order of
+// the additions is fixed, so every warp and block sums alike.
+template <int K>
+struct WarpSumShape {
+    static constexpr int P = K <= 1 ? 1 : K <= 2 ? 2 : K <= 4 ? 4 : K <= 8 ? 8 : K <= 16 ? 16 : K <= 32 ? 32 : 64;
+    static constexpr int LOGP = P == 1 ? 0 : P == 2 ? 1 : P == 4 ? 2 : P == 8 ? 3 : P == 16 ? 4 : P == 32 ? 5 : 6;
+    static constexpr int LT = LOGP < 5 ? LOGP : 5;
+    static constexpr int CF = P >> LT;
+};
+
+template <int K>
+__device__ __forceinline__ void warp_sum_transposed(const double (&in)[K], double (&out)[WarpSumShape<K>::CF]) {
+    using S = WarpSumShape<K>;
+    static_assert(K <= 64, "at most 64 values per reduction");
+    double v[S::P];
+#pragma unroll
+    for (int k = 0; k < S::P; ++k) v[k] = k < K ? in[k] : 0.0;
+    const int lane = threadIdx.x & 31;
+    int cnt = S::P;
+#pragma unroll
+    for (int lvl = 0; lvl < 5; ++lvl) {
+        const int o = 16 >> lvl;
+        if (lvl < S::LT) {
+            const bool up = (lane & o) != 0;
+            const int h = S::P >> (lvl + 1);
+#pragma unroll
+            for (int j = 0; j < S::P / 2; ++j)
+                if (j < h) {
+                    const double keep = up ? v[j + h] : v[j];
+                    const double send = up ? v[j] : v[j + h];
+                    v[j] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+                }
+            cnt = h;
+        } else {
+            v[0] += __shfl_xor_sync(0xffffffffu, v[0], o);
+        }
+    }
+    (void)cnt;
+#pragma unroll
+    for (int j = 0; j < S::CF; ++j) out[j] = v[j];
+}
+
+// Writes the warp totals of warp_sum_transposed to sm.warp[warp][k].
+template <int K>
+__device__ __forceinline__ void warp_totals_to_smem(const double (&t)[WarpSumShape<K>::CF], RedSmem &sm) {
+    using S = WarpSumShape<K>;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int sh = 5 - S::LT;
+    if ((lane & ((1 << sh) - 1)) == 0) {
+        const int base = (lane >> sh) * S::CF;
+#pragma unroll
+        for (int j = 0; j < S::CF; ++j)
+            if (base + j < K) sm.warp[warp][base + j] = t[j];
+    }
+}
+
+// Cross-warp stage: the per-warp totals sm.warp[w][k] (w < nw) are summed in
+// a fixed butterfly order by warp 0 and stored to sm.bcast[k].  Lanes are
+// packed (k, w) so that one FP64 instruction serves 32 / nw entries.
+template <int K>
+__device__ __forceinline__ void warp0_sum_warps(RedSmem &sm) {
+    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const int per = 32 / nw;                  // entries per warp instruction
+    const int k_in = lane / nw, w = lane % nw;
+    for (int k0 = 0; k0 < K; k0 += per) {
+        const int k = k0 + k_in;
+        double t = (k < K && k_in < per) ? sm.warp[w][k] : 0.0;
+        for (int o = nw >> 1; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (w == 0 && k < K && k_in < per) sm.bcast[k] = t;
+    }
+}
+
+// Sum of v over the block in a fixed order; the result is returned in v on
+// every thread.
 template <int K>
 __device__ __forceinline__ void block_sum(double (&v)[K], RedSmem &sm) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-#pragma unroll
-    for (int k = 0; k < K; ++k)
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
-    if (lane == 0)
-#pragma unroll
-        for (int k = 0; k < K; ++k) sm.warp[warp][k] = v[k];
+    double t[WarpSumShape<K>::CF];
+    warp_sum_transposed<K>(v, t);
+    warp_totals_to_smem<K>(t, sm);
     __syncthreads();
-    // warp w sums the entries k = w, w + nw, ... (each in one fixed order)
-    for (int k = warp; k < K; k += nw) {
-        double t = lane < nw ? sm.warp[lane][k] : 0.0;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-        if (lane == 0) sm.bcast[k] = t;
-    }
+    if ((threadIdx.x >> 5) == 0) warp0_sum_warps<K>(sm);
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < K; ++k) v[k] = sm.bcast[k];
@@ -149,22 +220,27 @@ struct GridTeam {
 
     template <int K>
     __device__ bool reduce(double (&v)[K]) {
-        block_sum<K>(v, *sm);
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+        double t[WarpSumShape<K>::CF];
+        warp_sum_transposed<K>(v, t);
+        warp_totals_to_smem<K>(t, *sm);
+        __syncthreads();
         slot ^= 1;
         double *P = partials + (size_t)slot * kMaxRed * nblocks;
-        if (threadIdx.x == 0)
-#pragma unroll
-            for (int k = 0; k < K; ++k) P[(size_t)k * nblocks + blockIdx.x] = v[k];
+        if (warp == 0) {
+            warp0_sum_warps<K>(*sm);
+            __syncwarp();
+            for (int k = lane; k < K; k += 32) P[(size_t)k * nblocks + blockIdx.x] = sm->bcast[k];
+        }
         if (!sync()) return false;
         // warp w sums the per-block partials of entries k = w, w + nw, ...;
         // the loads of different entries are in flight together
-        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
         for (int k = warp; k < K; k += nw) {
-            double t = 0.0;
-            for (int b = lane; b < nblocks; b += 32) t += __ldcg(P + (size_t)k * nblocks + b);
+            double u = 0.0;
+            for (int b = lane; b < nblocks; b += 32) u += __ldcg(P + (size_t)k * nblocks + b);
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-            if (lane == 0) sm->bcast[k] = t;
+            for (int o = 16; o > 0; o >>= 1) u += __shfl_xor_sync(0xffffffffu, u, o);
+            if (lane == 0) sm->bcast[k] = u;
         }
         __syncthreads();
 #pragma unroll
@@ -174,16 +250,18 @@ struct GridTeam {
     }
 };
 
+constexpr int kMaxCluster = 16;
+
 // The CTAs of one thread-block cluster (all co-scheduled by the hardware).
-// Barriers are the hardware cluster barrier; a reduction writes each CTA's
-// block sum to its own shared memory, and after the cluster barrier every
-// CTA reads all of them through distributed shared memory in rank order, so
-// all CTAs obtain the same bits.  Two exchange slots alternate: a CTA can
-// only overwrite slot s after every CTA has passed the barrier that follows
-// its last read of s.
+// Barriers are the hardware cluster barrier.  A reduction pushes each CTA's
+// block totals into every CTA's exchange buffer (remote shared-memory
+// stores, no round trip), and after the cluster barrier every CTA sums the
+// buffer's rows in rank order, so all CTAs obtain the same bits.  Two
+// exchange slots alternate: a CTA can only overwrite slot s after every CTA
+// has passed the barrier that follows its last read of s.
 struct ClusterTeam {
     RedSmem *sm;
-    double *xch;                  // this CTA's [2][kMaxRed] exchange buffer (shared memory)
+    double *xch;                  // this CTA's [2][kMaxCluster][kMaxRed] exchange buffer (shared memory)
     unsigned rank, size;
     int slot;
 
@@ -197,25 +275,32 @@ struct ClusterTeam {
     }
     template <int K>
     __device__ bool reduce(double (&v)[K]) {
-        block_sum<K>(v, *sm);
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+        double t[WarpSumShape<K>::CF];
+        warp_sum_transposed<K>(v, t);
+        warp_totals_to_smem<K>(t, *sm);
+        __syncthreads();
         slot ^= 1;
-        double *mine = xch + slot * kMaxRed;
-        if (threadIdx.x == 0)
-#pragma unroll
-            for (int k = 0; k < K; ++k) mine[k] = v[k];
-        cluster_barrier();
-        if (threadIdx.x < K) {
-            const int k = threadIdx.x;
-            const uint32_t local = (uint32_t)__cvta_generic_to_shared(mine + k);
-            double t = 0.0;
-            for (unsigned r = 0; r < size; ++r) {
+        double *buf = xch + (size_t)slot * kMaxCluster * kMaxRed;
+        if (warp == 0) {
+            warp0_sum_warps<K>(*sm);
+            __syncwarp();
+            for (int q = lane; q < (int)size * K; q += 32) {
+                const unsigned r = (unsigned)(q / K);
+                const int k = q - (int)r * K;
+                const uint32_t local = (uint32_t)__cvta_generic_to_shared(buf + rank * kMaxRed + k);
                 uint32_t remote;
                 asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(local), "r"(r));
-                double x;
-                asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(x) : "r"(remote) : "memory");
-                t += x;
+                asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(remote), "d"(sm->bcast[k]) : "memory");
             }
-            sm->bcast[k] = t;
+        }
+        cluster_barrier();
+        // rows of the exchange buffer summed in rank order (butterfly over
+        // the cluster's lanes; size is a power of two)
+        for (int k = warp; k < K; k += nw) {
+            double u = lane < (int)size ? buf[lane * kMaxRed + k] : 0.0;
+            for (int o = (int)size >> 1; o > 0; o >>= 1) u += __shfl_xor_sync(0xffffffffu, u, o);
+            if (lane == 0) sm->bcast[k] = u;
         }
         __syncthreads();
 #pragma unroll

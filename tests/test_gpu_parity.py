@@ -159,6 +159,32 @@ def test_qp_steady_2d_variants(opts):
         assert info["refinements"] >= 1 and info["spmv"] > info["spmv64"]
 
 
+@pytest.mark.parametrize("variant", [0, 1, 2])
+@pytest.mark.parametrize("prec", [P.NN_PREC_FP64, P.NN_PREC_MIXED])
+def test_cg_variants_reach_the_oracle_solution(variant, prec, monkeypatch):
+    """Every CG form of the face phase (textbook, Chronopoulos-Gear,
+    pipelined) gives the oracle's solution, steady and transient."""
+    monkeypatch.setenv("NNQP_CG_VARIANT", str(variant))
+    spec = I.config1_steady_2d(n=40)
+    s, c, info = solve_gpu(spec, rtol=1e-10, precision=prec)
+    assert info["status"] == 0, info
+    red, b, x_ref, _ = oracle_solution(spec)
+    compare_solution(c[red.free], x_ref, red.A, b, spec.lo, spec.hi)
+    spec = I.config2_transient_3d(n=8, nsteps=3)
+    st = gpu_system(spec)
+    c0 = torch.tensor(spec.c0, device=DEV)
+    cf = torch.zeros_like(c0)
+    hist = torch.zeros(spec.nsteps * spec.n_nodes, dtype=torch.float64, device=DEV)
+    infos = P.nn_transient(st, c0, spec.nsteps, cf, hist, P.solve_opts(rtol=1e-11, precision=prec))
+    assert all(i["status"] == 0 for i in infos)
+    H = hist.cpu().numpy().reshape(spec.nsteps, -1)
+    asm, red = oracle_reduced(spec)
+    ref = O.transient(red, spec.c0, spec.lo, spec.hi, spec.nsteps)
+    for n in range(spec.nsteps):
+        b = red.rhs(ref[n - 1] if n else spec.c0)
+        compare_solution(H[n][red.free], ref[n][red.free], red.A, b, spec.lo, spec.hi)
+
+
 @pytest.mark.parametrize("case", ["2d_n4_lower", "2d_n4_box", "3d_n3_lower", "2d_4x5_lower"])
 @pytest.mark.parametrize("prec", [P.NN_PREC_FP64, P.NN_PREC_MIXED])
 def test_qp_matches_bruteforce(case, prec):
@@ -230,16 +256,19 @@ def test_not_converged_returns_feasible_iterate():
 
 # ------------------------------------------------------------------ transient
 
-@pytest.mark.parametrize("extrapolate", [0, 1])
-def test_transient_small_matches_oracle_trajectory(extrapolate):
+@pytest.mark.parametrize("extrapolate,prec", [(0, "fp64"), (1, "fp64"), (1, "mixed")])
+def test_transient_small_matches_oracle_trajectory(extrapolate, prec):
     """Either first iterate (c^(n), or the projected extrapolation
-    2 c^(n) - c^(n-1)) reaches the oracle's step solution."""
+    2 c^(n) - c^(n-1)) and either precision (FP64, or FP32 inner solves
+    refined in FP64) reach the oracle's step solution."""
     spec = I.config2_transient_3d(n=10, nsteps=8)
     s = gpu_system(spec)
     c0 = torch.tensor(spec.c0, device=DEV)
     cf = torch.zeros_like(c0)
     hist = torch.zeros(spec.nsteps * spec.n_nodes, dtype=torch.float64, device=DEV)
-    infos = P.nn_transient(s, c0, spec.nsteps, cf, hist, P.solve_opts(rtol=1e-11, extrapolate=extrapolate))
+    p = P.NN_PREC_MIXED if prec == "mixed" else P.NN_PREC_FP64
+    infos = P.nn_transient(s, c0, spec.nsteps, cf, hist,
+                           P.solve_opts(rtol=1e-11, extrapolate=extrapolate, precision=p))
     assert all(i["status"] == 0 for i in infos)
     H = hist.cpu().numpy().reshape(spec.nsteps, -1)
     assert np.array_equal(H[-1], cf.cpu().numpy())

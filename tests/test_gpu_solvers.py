@@ -116,11 +116,14 @@ def test_batch_equals_single_block_solve_alone():
         assert torch.equal(alone, cs[k])
 
 
-@pytest.mark.parametrize("shape", ["256x4", "256x8", "256x16"])
-def test_batch_cluster_shapes_match_oracle(shape, monkeypatch):
+@pytest.mark.parametrize("shape,variant", [("256x4", 0), ("256x8", 0), ("256x16", 0), ("256x8", 1), ("256x8", 2),
+                                           ("256x1", 2)])
+def test_batch_cluster_shapes_match_oracle(shape, variant, monkeypatch):
     """One thread-block cluster per instance (hardware cluster barrier,
-    reductions through distributed shared memory) gives oracle parity."""
+    reductions through distributed shared memory) gives oracle parity, with
+    each CG form of the face phase."""
     monkeypatch.setenv("NNQP_BATCH_SHAPE", shape)
+    monkeypatch.setenv("NNQP_BATCH_CG_VARIANT", str(variant))
     insts, systems = _batch(count=12, nmin=16, nmax=48)
     cs = [torch.zeros(sp.n_nodes, dtype=torch.float64, device=DEV) for sp in insts]
     for prec in (P.NN_PREC_FP64, P.NN_PREC_MIXED):

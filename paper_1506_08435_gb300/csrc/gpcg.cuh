@@ -80,8 +80,8 @@ __device__ __forceinline__ bool team_sum(Team &T, const V (&acc)[K], double (&ou
 // scalar division repeated by all warps of a block costs as much as the
 // reduction itself.
 template <class Team, typename V, int K, int M, class F>
-__device__ __forceinline__ bool team_sum_scalar(Team &T, const V (&acc)[K], double (&out)[M], F &&f) {
-    double d[K];
+__device__ __forceinline__ bool team_sum_scalar(Team &T, const V (&acc)[K], double (&d)[K], double (&out)[M],
+                                                F &&f) {
 #pragma unroll
     for (int k = 0; k < K; ++k) d[k] = (double)acc[k];
     if (!T.reduce(d)) return false;
@@ -102,35 +102,59 @@ __device__ __forceinline__ bool team_sum_scalar(Team &T, const V (&acc)[K], doub
 
 __device__ __forceinline__ bool flag_set(double f) { return __double_as_longlong(f) != 0; }
 
-// Scalar step of the Chronopoulos-Gear / pipelined CG iterations: from the
-// sums d = (gamma', delta', r'r, crossings) and the current alpha, beta,
-// gamma, maxdec, decides whether the CG phase stops and computes the next
-// coefficients.  r = (stop, alpha, beta, gamma, maxdec).
-__device__ __forceinline__ void cg_scalar_step(const double (&d)[4], double (&r)[5], double alpha, double beta,
-                                               double gamma, double maxdec, double eta2, double ftol2,
-                                               bool count_cross) {
-    const double dec = 0.5 * alpha * gamma;
-    if (dec > maxdec) maxdec = dec;
+// State of the Chronopoulos-Gear / pipelined CG recurrences.  The
+// reciprocals 1/alpha and 1/gamma are carried so that a step needs one
+// dependent division (FP64 latency on GB300 is tens of cycles per
+// operation, and a division is a chain of them).
+struct CgScalars {
+    double alpha, beta, gamma, ialpha, igamma, maxdec;
+};
+
+// From the sums d = (gamma', delta', r'r, crossings) decides whether the CG
+// phase stops (returns 1.0 in r[0]) and computes the next coefficients:
+//   beta' = gamma'/gamma, alpha' = gamma' / (delta' - beta' gamma'/alpha).
+// r = (stop, alpha, beta, gamma, ialpha, igamma, maxdec).
+__device__ __forceinline__ void cg_scalar_step(const double (&d)[4], double (&r)[7], const CgScalars &c,
+                                               double eta2, double ftol2, bool count_cross) {
+    const double dec = 0.5 * c.alpha * c.gamma;
+    const double maxdec = dec > c.maxdec ? dec : c.maxdec;
     const double gnew = d[0];
-    double stop = 0.0;
-    if ((count_cross && d[3] > 0.0) || dec <= eta2 * maxdec || d[2] <= ftol2 || !(gnew > 0.0)) {
-        stop = 1.0;
-    } else {
-        const double bnew = gnew / gamma;
-        const double den = d[1] - bnew * gnew / alpha;
-        if (!(den > 0.0)) {
-            stop = 1.0;
-        } else {
-            alpha = gnew / den;
-            beta = bnew;
-            gamma = gnew;
-        }
-    }
-    r[0] = stop;
-    r[1] = alpha;
-    r[2] = beta;
+    const double ig = 1.0 / gnew;                 // independent of the chain below
+    const double bnew = gnew * c.igamma;
+    const double den = fma(-bnew * gnew, c.ialpha, d[1]);
+    const double anew = gnew / den;
+    const bool stop = (count_cross && d[3] > 0.0) || dec <= eta2 * maxdec || d[2] <= ftol2 || !(gnew > 0.0) ||
+                      !(den > 0.0);
+    r[0] = stop ? 1.0 : 0.0;
+    r[1] = stop ? c.alpha : anew;
+    r[2] = stop ? c.beta : bnew;
+    r[3] = stop ? c.gamma : gnew;
+    r[4] = stop ? c.ialpha : den * ig;
+    r[5] = stop ? c.igamma : ig;
+    r[6] = maxdec;
+}
+
+// First coefficients of a CG phase from gamma = r'u and delta = w'u:
+// r = (stop, alpha, beta = 0, gamma, ialpha, igamma, maxdec = 0).
+__device__ __forceinline__ void cg_scalar_start(const double (&d)[2], double (&r)[7]) {
+    const double gamma = d[0], delta = d[1];
+    const bool stop = !(gamma > 0.0) || !(delta > 0.0);
+    r[0] = stop ? 1.0 : 0.0;
+    r[1] = gamma / delta;
+    r[2] = 0.0;
     r[3] = gamma;
-    r[4] = maxdec;
+    r[4] = delta / gamma;
+    r[5] = 1.0 / gamma;
+    r[6] = 0.0;
+}
+
+__device__ __forceinline__ void cg_take(CgScalars &c, const double (&o)[7]) {
+    c.alpha = o[1];
+    c.beta = o[2];
+    c.gamma = o[3];
+    c.ialpha = o[4];
+    c.igamma = o[5];
+    c.maxdec = o[6];
 }
 
 template <typename V>
@@ -210,16 +234,21 @@ __device__ int gpcg_solve(Team &T, const Rows &R, const Op &A, const Bounds<V> &
                 st.vec += 3;
                 if (!T.sync()) return ST_TIMEOUT;
                 V a1[1] = {zero};
-                double d1[1];
+                double d1[1], oc[2];
                 A.apply(R, v.p, [&](int64_t i, V ap) { a1[0] += v.p[i] * ap; });
-                if (!team_sum(T, a1, d1)) return ST_TIMEOUT;
+                const double gp2 = st.gp2;
+                if (!team_sum_scalar(T, a1, d1, oc, [&](const double (&d)[1], double (&r)[2]) {
+                        r[0] = d[0] > 0.0 ? 1.0 : 0.0;
+                        r[1] = gp2 / d[0];
+                    }))
+                    return ST_TIMEOUT;
                 ++st.spmv;
                 st.fl += 2;
-                if (!(d1[0] > 0.0)) break;
-                alpha = st.gp2 / d1[0];
+                if (!flag_set(oc[0])) break;
+                alpha = oc[1];
             }
             bool accepted = false;
-            double d2[6];
+            double d2[6], o2[5];
             for (int ls = 0; ls < 48 && st.spmv < C.max_spmv; ++ls) {
                 V a2[6] = {zero, zero, zero, zero, zero, zero};
                 const V va = (V)alpha;
@@ -242,15 +271,29 @@ __device__ int gpcg_solve(Team &T, const Rows &R, const Op &A, const Bounds<V> &
                     a2[4] += si * si;
                     a2[5] += si * yi;
                 });
-                if (!team_sum(T, a2, d2)) return ST_TIMEOUT;
+                // Armijo test; on acceptance the Barzilai-Borwein length s's/s'y
+                // for the next step and the phase's stall test (no change of the
+                // active set, or a decrease below eta1 times the best)
+                const double al = alpha, md = maxdec;
+                if (!team_sum_scalar(T, a2, d2, o2, [&](const double (&d)[6], double (&r)[5]) {
+                        const bool acc = 0.5 * d[2] <= C.mu * d[0];
+                        const double dec = -0.5 * d[2];
+                        const double mdn = dec > md ? dec : md;
+                        r[0] = acc ? 1.0 : 0.0;
+                        r[1] = 0.5 * al;
+                        r[2] = d[5] > 0.0 ? d[4] / d[5] : 0.0;
+                        r[3] = mdn;
+                        r[4] = (d[3] <= tol2 || d[1] == 0.0 || dec <= C.eta1 * mdn) ? 1.0 : 0.0;
+                    }))
+                    return ST_TIMEOUT;
                 ++st.spmv;
                 st.vec += 7;
                 st.fl += 17;
-                if (0.5 * d2[2] <= C.mu * d2[0]) {
+                if (flag_set(o2[0])) {
                     accepted = true;
                     break;
                 }
-                alpha *= 0.5;
+                alpha = o2[1];
             }
             if (!accepted) {
                 bb = 0.0;
@@ -259,11 +302,9 @@ __device__ int gpcg_solve(Team &T, const Rows &R, const Op &A, const Bounds<V> &
             V *t = v.x; v.x = v.w; v.w = t;
             t = v.g; v.g = v.gw; v.gw = t;
             st.gp2 = d2[3];
-            bb = d2[5] > 0.0 ? d2[4] / d2[5] : 0.0;
-            const double dec = -0.5 * d2[2];
-            if (dec > maxdec) maxdec = dec;
-            if (st.gp2 <= tol2 || st.spmv >= C.max_spmv) break;
-            if (d2[1] == 0.0 || dec <= C.eta1 * maxdec) break;
+            bb = o2[2];
+            maxdec = o2[3];
+            if (flag_set(o2[4]) || st.spmv >= C.max_spmv) break;
         }
         if (st.gp2 <= tol2 || st.spmv >= C.max_spmv || !isfinite(st.gp2)) continue;
         // ------------------------------------------------ CG on faces
@@ -296,15 +337,17 @@ __device__ int gpcg_solve(Team &T, const Rows &R, const Op &A, const Bounds<V> &
                     a3[0] += v.r[i] * ui;
                     a3[1] += wi * ui;
                 });
-                if (!team_sum(T, a3, d3)) return ST_TIMEOUT;
+                double o3[7];
+                if (!team_sum_scalar(T, a3, d3, o3, [&](const double (&d)[2], double (&r)[7]) { cg_scalar_start(d, r); }))
+                    return ST_TIMEOUT;
                 ++st.spmv;
                 st.vec += 3;
                 st.fl += 4;
-                double gamma = d3[0], delta = d3[1];
-                if (!(gamma > 0.0) || !(delta > 0.0)) break;
-                double alpha = gamma / delta, beta = 0.0, maxdec = 0.0;
+                if (flag_set(o3[0])) break;
+                CgScalars cs;
+                cg_take(cs, o3);
                 for (int k = 0; k < C.cg_max; ++k) {
-                    const V va = (V)alpha, vb = (V)beta;
+                    const V va = (V)cs.alpha, vb = (V)cs.beta;
                     V a4[4] = {zero, zero, zero, zero};   // gamma, delta, r'r, bound crossings
                     R.each([&](int64_t i) {
                         V pi = v.z[i] + vb * v.p[i];
@@ -332,20 +375,17 @@ __device__ int gpcg_solve(Team &T, const Rows &R, const Op &A, const Bounds<V> &
                         a4[1] += wi * ui;
                         a4[2] += ri * ri;
                     });
-                    double o[5];
-                    if (!team_sum_scalar(T, a4, o, [&](const double (&d)[4], double (&r)[5]) {
-                            cg_scalar_step(d, r, alpha, beta, gamma, maxdec, C.eta2, ftol2, count_cross);
+                    double d4[4], o[7];
+                    if (!team_sum_scalar(T, a4, d4, o, [&](const double (&d)[4], double (&r)[7]) {
+                            cg_scalar_step(d, r, cs, C.eta2, ftol2, count_cross);
                         }))
                         return ST_TIMEOUT;
                     ++st.spmv;
                     ++st.cg;
                     st.vec += 3;
                     st.fl += 6;
-                    maxdec = o[4];
                     if (flag_set(o[0]) || st.spmv >= C.max_spmv) break;
-                    alpha = o[1];
-                    beta = o[2];
-                    gamma = o[3];
+                    cg_take(cs, o);
                 }
             } else if ((CGV >= 0 ? CGV : C.cg_variant) == 2) {
                 // Pipelined form (Ghysels & Vanroose, Parallel Comput. 40, 2014)
@@ -386,15 +426,17 @@ __device__ int gpcg_solve(Team &T, const Rows &R, const Op &A, const Bounds<V> &
                     a3[0] += ri * ui;
                     a3[1] += wi * ui;
                 });
-                if (!team_sum(T, a3, d3)) return ST_TIMEOUT;
+                double o3[7];
+                if (!team_sum_scalar(T, a3, d3, o3, [&](const double (&d)[2], double (&r)[7]) { cg_scalar_start(d, r); }))
+                    return ST_TIMEOUT;
                 ++st.spmv;
                 st.vec += 5;
                 st.fl += 6;
-                double gamma = d3[0], delta = d3[1];
-                if (!(gamma > 0.0) || !(delta > 0.0)) break;
-                double alpha = gamma / delta, beta = 0.0, maxdec = 0.0;
+                if (flag_set(o3[0])) break;
+                CgScalars cs;
+                cg_take(cs, o3);
                 for (int k = 0; k < C.cg_max; ++k) {
-                    const V va = (V)alpha, vb = (V)beta;
+                    const V va = (V)cs.alpha, vb = (V)cs.beta;
                     V a4[4] = {zero, zero, zero, zero};   // gamma, delta, r'r, bound crossings
                     A.apply(R, mc, [&](int64_t i, V an) {
                         V ni = v.fm[i] ? an : zero;
@@ -422,20 +464,17 @@ __device__ int gpcg_solve(Team &T, const Rows &R, const Op &A, const Bounds<V> &
                             a4[3] += (xs < B.l(i) || xs > B.h(i)) ? one : zero;
                         }
                     });
-                    double o[5];
-                    if (!team_sum_scalar(T, a4, o, [&](const double (&d)[4], double (&r)[5]) {
-                            cg_scalar_step(d, r, alpha, beta, gamma, maxdec, C.eta2, ftol2, count_cross);
+                    double d4[4], o[7];
+                    if (!team_sum_scalar(T, a4, d4, o, [&](const double (&d)[4], double (&r)[7]) {
+                            cg_scalar_step(d, r, cs, C.eta2, ftol2, count_cross);
                         }))
                         return ST_TIMEOUT;
                     ++st.spmv;
                     ++st.cg;
                     st.vec += count_cross ? 15 : 14;
                     st.fl += 21;
-                    maxdec = o[4];
                     if (flag_set(o[0]) || st.spmv >= C.max_spmv) break;
-                    alpha = o[1];
-                    beta = o[2];
-                    gamma = o[3];
+                    cg_take(cs, o);
                     V *t = mc;
                     mc = mn;
                     mn = t;
@@ -513,7 +552,7 @@ __device__ int gpcg_solve(Team &T, const Rows &R, const Op &A, const Bounds<V> &
             // projected search along the CG step s
             double alpha = 1.0;
             bool accepted = false;
-            double d6[5];
+            double d6[5], o6[3];
             for (int ls = 0; ls < 48; ++ls) {
                 V a6[5] = {zero, zero, zero, zero, zero};
                 const V va = (V)alpha;
@@ -533,22 +572,29 @@ __device__ int gpcg_solve(Team &T, const Rows &R, const Op &A, const Bounds<V> &
                     a6[3] += gp * gp;
                     a6[4] += ((wi <= l || wi >= h) && gp != zero) ? one : zero;
                 });
-                if (!team_sum(T, a6, d6)) return ST_TIMEOUT;
+                // Armijo test; after acceptance the face loop ends on convergence
+                // or on a non-binding active entry (back to gradient projection)
+                const double al = alpha;
+                if (!team_sum_scalar(T, a6, d6, o6, [&](const double (&d)[5], double (&r)[3]) {
+                        r[0] = 0.5 * d[2] <= C.mu * d[0] ? 1.0 : 0.0;
+                        r[1] = (d[3] <= tol2 || !isfinite(d[3]) || d[4] > 0.0) ? 1.0 : 0.0;
+                        r[2] = 0.5 * al;
+                    }))
+                    return ST_TIMEOUT;
                 ++st.spmv;
                 st.vec += 7;
                 st.fl += 11;
-                if (0.5 * d6[2] <= C.mu * d6[0]) {
+                if (flag_set(o6[0])) {
                     accepted = true;
                     break;
                 }
-                alpha *= 0.5;
+                alpha = o6[2];
             }
             if (!accepted) break;
             V *t = v.x; v.x = v.w; v.w = t;
             t = v.g; v.g = v.gw; v.gw = t;
             st.gp2 = d6[3];
-            if (st.gp2 <= tol2 || st.spmv >= C.max_spmv || !isfinite(st.gp2)) break;
-            if (d6[4] > 0.0) break;  // a non-binding active entry: back to gradient projection
+            if (flag_set(o6[1]) || st.spmv >= C.max_spmv) break;
         }
     }
     return status;

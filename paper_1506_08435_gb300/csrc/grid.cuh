@@ -119,8 +119,11 @@ __device__ bool step_outputs(Team &T, const Rows &R, const GridArgs &a, const do
 
 // One instantiation per (format, mode) so that each kernel carries only the
 // code of its own path (register allocation is per kernel).
-template <int FMT, int MODE, int CGV>
-__global__ void __launch_bounds__(kSolveThreads, mode_min_blocks(MODE)) k_solve_grid(GridArgs a) {
+// TPB threads per block: 256 (several blocks per SM on large systems) or 512
+// (one block per SM on mid-size systems: one slice per warp, so the loads of
+// a pass are all in flight at once).
+template <int FMT, int MODE, int CGV, int TPB>
+__global__ void __launch_bounds__(TPB, TPB >= 512 ? 1 : mode_min_blocks(MODE)) k_solve_grid(GridArgs a) {
     __shared__ RedSmem sm;
     GridTeam T{a.bar, a.partials, (int)gridDim.x + a.bar_extra, a.timeout_ns, 0, 0, &sm};
     const Rows R = rows_of_block(a.n, a.nslices, blockIdx.x, gridDim.x);
@@ -193,11 +196,12 @@ __global__ void __launch_bounds__(kSolveThreads, mode_min_blocks(MODE)) k_solve_
 
 using GridKernel = void (*)(GridArgs);
 
-// Kernel of one mode for format fmt (NN_FMT_SELL / NN_FMT_CSR) and CG
-// variant cgv (0, 1, 2); nullptr if that combination is not built.
-GridKernel grid_kernel_steady(int fmt, int cgv);
-GridKernel grid_kernel_transient(int fmt, int cgv);
-GridKernel grid_kernel_mixed(int fmt, int cgv);
-GridKernel grid_kernel_mixed_transient(int fmt, int cgv);
+// Kernel of one mode for format fmt (NN_FMT_SELL / NN_FMT_CSR), CG variant
+// cgv (0, 1, 2) and threads per block tpb (256, 512); nullptr if that
+// combination is not built.
+GridKernel grid_kernel_steady(int fmt, int cgv, int tpb);
+GridKernel grid_kernel_transient(int fmt, int cgv, int tpb);
+GridKernel grid_kernel_mixed(int fmt, int cgv, int tpb);
+GridKernel grid_kernel_mixed_transient(int fmt, int cgv, int tpb);
 
 }  // namespace nnqp

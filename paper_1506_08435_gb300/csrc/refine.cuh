@@ -36,10 +36,24 @@ struct MixedStats {
 // once per call instead of competing with the solver's inner loops for
 // registers (the grid kernels, compiled for 80 or 128 registers).  Without
 // SPLIT they are inlined (the batch kernels, which have 255 registers).
+// The callee works on register copies of everything passed by reference:
+// through the references the objects live in the caller's stack frame, and
+// every global store could alias them, so each use would reload them.
 template <class Team, class Op, typename V, int CGV>
 __device__ __noinline__ int gpcg_call_split(Team &T, const Rows &R, const Op &A, const Bounds<V> &B,
                                             GpcgVecs<V> &v, const GpcgCtl &C, GpcgStats &st) {
-    return gpcg_solve<Team, Op, V, CGV>(T, R, A, B, v, C, st);
+    Team t = T;
+    GpcgVecs<V> w = v;
+    GpcgStats s = st;
+    const Rows r = R;
+    const Op a = A;
+    const Bounds<V> b = B;
+    const GpcgCtl c = C;
+    const int status = gpcg_solve<Team, Op, V, CGV>(t, r, a, b, w, c, s);
+    T = t;
+    v = w;
+    st = s;
+    return status;
 }
 
 template <bool SPLIT, class Team, class Op, typename V, int CGV>

@@ -164,18 +164,18 @@ int device_sms() {
 }
 
 template <typename K>
-int max_coresident(K kern) {
+int max_coresident(K kern, int tpb = kSolveThreads) {
     int per = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, kSolveThreads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, tpb, 0);
     return std::max(per, 1) * device_sms();
 }
 
-GridKernel grid_kernel(int mode, int fmt, int cgv) {
+GridKernel grid_kernel(int mode, int fmt, int cgv, int tpb = kSolveThreads) {
     switch (mode) {
-        case MODE_TRANSIENT: return grid_kernel_transient(fmt, cgv);
-        case MODE_MIXED: return grid_kernel_mixed(fmt, cgv);
-        case MODE_MIXED_TR: return grid_kernel_mixed_transient(fmt, cgv);
-        default: return grid_kernel_steady(fmt, cgv);
+        case MODE_TRANSIENT: return grid_kernel_transient(fmt, cgv, tpb);
+        case MODE_MIXED: return grid_kernel_mixed(fmt, cgv, tpb);
+        case MODE_MIXED_TR: return grid_kernel_mixed_transient(fmt, cgv, tpb);
+        default: return grid_kernel_steady(fmt, cgv, tpb);
     }
 }
 
@@ -296,19 +296,30 @@ nn_status run_grid(nn_system *s, const nn_solve_opts *o, int mode, int nsteps, c
     }
     a.predict = o->extrapolate;
     if (mode_transient(mode) && a.predict) NN_TRY(S.a.alloc(&a.xprev, n, st));
-    GridKernel kern = lbfgs ? k_lbfgs_grid : grid_kernel(mode, fmt, a.ctl.cg_variant);
+    // Grid: one slice per warp at least.  Systems that a grid of one block
+    // per SM covers in a few slices per warp run one block per SM (fewer
+    // barrier arrivals) of 512 threads (one slice per warp: all loads of a
+    // pass in flight at once); larger systems run the full co-resident grid
+    // of 256-thread blocks (more loads in flight per SM).
+    const int sms = device_sms();
+    const int64_t slices = s->A64.nslices;
+    int tpb = kSolveThreads;
+    if (!lbfgs && slices <= (int64_t)4 * 8 * sms && slices > (int64_t)8 * sms / 2) tpb = 512;
+    if (const char *e = getenv("NNQP_GRID_THREADS")) tpb = atoi(e);
+    GridKernel kern = lbfgs ? k_lbfgs_grid : grid_kernel(mode, fmt, a.ctl.cg_variant, tpb);
+    if (!kern && !lbfgs && tpb != kSolveThreads) {
+        tpb = kSolveThreads;
+        kern = grid_kernel(mode, fmt, a.ctl.cg_variant, tpb);
+    }
+    if (lbfgs) tpb = kSolveThreads;
     if (!kern) {
         set_error("CG variant %d is not available for this mode and format", a.ctl.cg_variant);
         return NN_ERR_INVALID_ARG;
     }
-    const int maxg = max_coresident(kern);
-    // one slice per warp at least; grids of up to one block per SM while that
-    // covers the rows in a few slices per warp (fewer barrier arrivals), the
-    // full co-resident grid for large systems (more loads in flight)
-    const int warps = kSolveThreads / 32;
-    const int64_t by_rows = (s->A64.nslices + warps - 1) / warps;
-    const int sms = device_sms();
-    int want = (int)std::min<int64_t>(by_rows, by_rows <= 4 * sms ? (int64_t)sms : (int64_t)maxg);
+    const int maxg = max_coresident(kern, tpb);
+    const int warps = tpb / 32;
+    const int64_t by_rows = (slices + warps - 1) / warps;
+    int want = (int)std::min<int64_t>(by_rows, slices <= (int64_t)4 * 8 * sms ? (int64_t)sms : (int64_t)maxg);
     want = std::min(want, maxg);
     if (o->grid_blocks > 0) want = std::min(o->grid_blocks, maxg);
     want = std::max(want, 1);
@@ -328,7 +339,7 @@ nn_status run_grid(nn_system *s, const nn_solve_opts *o, int mode, int nsteps, c
     NN_CUDA_TRY(cudaEventCreate(&e1));
     cudaEventRecord(e0, st);
     void *args[] = {&a};
-    cudaError_t le = cudaLaunchCooperativeKernel((void *)kern, dim3(want), dim3(kSolveThreads), args, 0, st);
+    cudaError_t le = cudaLaunchCooperativeKernel((void *)kern, dim3(want), dim3(tpb), args, 0, st);
     count_launch();
     if (le != cudaSuccess) {
         cudaEventDestroy(e0);

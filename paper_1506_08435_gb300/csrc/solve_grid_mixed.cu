@@ -3,12 +3,20 @@
 
 namespace nnqp {
 
-GridKernel grid_kernel_mixed(int fmt, int cgv) {
+GridKernel grid_kernel_mixed(int fmt, int cgv, int tpb) {
     if (fmt != NN_FMT_SELL) return nullptr;
+    if (tpb == 512) {
+        switch (cgv) {
+            case 1: return k_solve_grid<0, MODE_MIXED, 1, 512>;
+            case 2: return k_solve_grid<0, MODE_MIXED, 2, 512>;
+            default: return nullptr;
+        }
+    }
+    if (tpb != 256) return nullptr;
     switch (cgv) {
-        case 0: return k_solve_grid<0, MODE_MIXED, 0>;
-        case 1: return k_solve_grid<0, MODE_MIXED, 1>;
-        case 2: return k_solve_grid<0, MODE_MIXED, 2>;
+        case 0: return k_solve_grid<0, MODE_MIXED, 0, 256>;
+        case 1: return k_solve_grid<0, MODE_MIXED, 1, 256>;
+        case 2: return k_solve_grid<0, MODE_MIXED, 2, 256>;
         default: return nullptr;
     }
 }

@@ -3,18 +3,27 @@
 
 namespace nnqp {
 
-GridKernel grid_kernel_steady(int fmt, int cgv) {
+GridKernel grid_kernel_steady(int fmt, int cgv, int tpb) {
     if (fmt == NN_FMT_CSR) {
+        if (tpb != 256) return nullptr;
         switch (cgv) {
-            case 0: return k_solve_grid<1, MODE_STEADY, 0>;
-            case 1: return k_solve_grid<1, MODE_STEADY, 1>;
+            case 0: return k_solve_grid<1, MODE_STEADY, 0, 256>;
+            case 1: return k_solve_grid<1, MODE_STEADY, 1, 256>;
             default: return nullptr;
         }
     }
+    if (tpb == 512) {
+        switch (cgv) {
+            case 1: return k_solve_grid<0, MODE_STEADY, 1, 512>;
+            case 2: return k_solve_grid<0, MODE_STEADY, 2, 512>;
+            default: return nullptr;
+        }
+    }
+    if (tpb != 256) return nullptr;
     switch (cgv) {
-        case 0: return k_solve_grid<0, MODE_STEADY, 0>;
-        case 1: return k_solve_grid<0, MODE_STEADY, 1>;
-        case 2: return k_solve_grid<0, MODE_STEADY, 2>;
+        case 0: return k_solve_grid<0, MODE_STEADY, 0, 256>;
+        case 1: return k_solve_grid<0, MODE_STEADY, 1, 256>;
+        case 2: return k_solve_grid<0, MODE_STEADY, 2, 256>;
         default: return nullptr;
     }
 }

@@ -173,6 +173,19 @@ def oracle_sample(workload, budget_s=20.0, n=None):
 
 # ---------------------------------------------------------------- helpers
 
+def source_digest():
+    """SHA-256 over the library's kernel and host sources (names and bytes,
+    sorted by name): identifies the code an ncu summary was captured from."""
+    import hashlib
+    d = os.path.join(ROOT, "paper_1506_08435_gb300", "csrc")
+    h = hashlib.sha256()
+    for name in sorted(os.listdir(d)):
+        if name.endswith((".cu", ".cuh", ".h", ".cpp")):
+            h.update(name.encode())
+            h.update(open(os.path.join(d, name), "rb").read())
+    return h.hexdigest()[:16]
+
+
 def pinned_problem(P, torch, spec):
     """A Problem whose arrays are in pinned host memory (for the e2e leg)."""
     hp = P.Problem(spec)
@@ -317,6 +330,7 @@ def run_steady(P, torch, args, rank, dim):
     name = ("steady3d_n%d" % (args.n or 150)) if dim == 3 else ("steady2d_n%d" % (args.n or 50))
     return dict(times=times, infos=infos, kern_ms=[o[0]["time_ms"] for o in outs],
                 kern_bytes=[o[0]["bytes_algo"] for o in outs], units_per_step=1, e2e=e2e,
+                nnz_free=desc.get("nnz_free"), profile_scale_from="steady3d_n100" if dim == 3 else None,
                 h2d=hbytes + ch.numel() * 8, d2h=ch.numel() * 8, clocks=clocks, launches=launches,
                 config={"workload": name, "nodes": spec.n_nodes, "free": desc.get("n_free"),
                         "nnz_free": desc.get("nnz_free"), "rtol": args.rtol, "solver": args.solver,
@@ -349,6 +363,7 @@ def run_batch(P, torch, args, rank):
     launches = P.kernel_launches() - l0
     infos = [i for o in outs for i in o]
     return dict(times=times, infos=infos, kern_ms=[o[0]["time_ms"] for o in outs],
+                kernel_name="k_batch_cluster" if tuned % 100 > 1 else "k_batch",
                 kern_bytes=[sum(i["bytes_algo"] for i in o) for o in outs], units_per_step=count, e2e=None,
                 h2d=0, d2h=0, clocks=clocks, launches=launches,
                 config={"workload": "batch2d_%d" % count, "instances": count, "threads_per_block": tuned // 100, "ctas_per_instance": tuned % 100,
@@ -483,23 +498,43 @@ def main():
     kern_ms = float(np.mean(r["kern_ms"]))
     kern_bytes = float(np.mean(r["kern_bytes"]))
     achieved = kern_bytes / (kern_ms / 1e3) / 1e9
-    # DRAM bytes per launch of the solve kernel from the committed ncu summary
-    # of this workload (a line "dram_bytes_per_launch: N"), if there is one
-    tfile = os.path.join(ROOT, "profiles", "k_solve_grid_%s.md" % r["config"]["workload"])
-    traffic = None
+    # DRAM bytes per launch of the dominant kernel from the committed ncu
+    # summary of this workload and precision (a line "dram_bytes_per_launch:
+    # N"), used only while that summary's "source_digest:" line matches the
+    # kernel sources as they are now (counters of an older kernel are void)
+    traffic, traffic_src = None, "no ncu summary for this workload"
+    kname = r.get("kernel_name", "k_solve_grid")
+    tfile = os.path.join(ROOT, "profiles", "%s_%s_%s.md" % (kname, r["config"]["workload"], args.precision))
+    scaled = False
+    if not os.path.exists(tfile) and r.get("profile_scale_from"):
+        tfile = os.path.join(ROOT, "profiles", "%s_%s_%s.md" % (kname, r["profile_scale_from"], args.precision))
+        scaled = True
     if os.path.exists(tfile):
+        fields = {}
         for line in open(tfile):
-            if line.strip().startswith("dram_bytes_per_launch:"):
-                try:
-                    traffic = float(line.split(":", 1)[1].split()[0])
-                except ValueError:
-                    traffic = None
+            key = line.split(":", 1)[0].strip() if ":" in line else ""
+            if key in ("dram_bytes_per_launch", "source_digest", "products_per_launch", "nnz_free"):
+                v = line.split(":", 1)[1].strip()
+                fields[key] = v.split()[0] if v else ""
+        if fields.get("source_digest") != source_digest():
+            traffic_src = "kernel changed since the ncu capture in %s" % os.path.basename(tfile)
+        else:
+            try:
+                traffic = float(fields["dram_bytes_per_launch"])
+                traffic_src = "ncu capture, %s" % os.path.basename(tfile)
+                if scaled:
+                    spl = sum(i["spmv"] for i in r["infos"]) / args.steps
+                    traffic *= spl / float(fields["products_per_launch"]) * r["nnz_free"] / float(fields["nnz_free"])
+                    traffic_src = ("ncu capture of a smaller case (%s), scaled by products x nnz_free"
+                                   % os.path.basename(tfile))
+            except (KeyError, ValueError, TypeError):
+                traffic, traffic_src = None, "incomplete ncu summary %s" % os.path.basename(tfile)
     infos = r["infos"]
     line = {"metric": r["metric"], "value": value, "unit": r["unit"], "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": r["dtype"], "data": "synthetic", "config": r["config"],
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                         "frac": achieved / hbm_peak, "traffic": traffic,
+                         "frac": achieved / hbm_peak, "traffic": traffic, "traffic_source": traffic_src,
                          "kernel": "solve kernel (persistent, one launch per step)",
                          "kernel_ms": kern_ms, "algo_bytes_per_launch": kern_bytes, "peak_source": peak_src},
             "gpu_launches": r["launches"], "clocks": r["clocks"],

@@ -38,6 +38,30 @@ struct SellF64 {
         const double2 *v2 = reinterpret_cast<const double2 *>(val + base) + lane;
         double a0 = 0.0, a1 = 0.0;
         int k = 0;
+        // 8 entries per step: every column/value load of the step is issued
+        // before the gathers, and every gather before the FMAs, so a row's
+        // loads are in flight together (the bound on large systems is memory
+        // parallelism, not arithmetic)
+        for (; k + 8 <= w; k += 8) {
+            int2 c[4];
+            double2 v[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                c[j] = __ldg(c2 + 16 * (k + 2 * j));
+                v[j] = __ldg(v2 + 16 * (k + 2 * j));
+            }
+            double xv[8];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                xv[2 * j] = (double)x[c[j].x];
+                xv[2 * j + 1] = (double)x[c[j].y];
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                a0 = fma(v[j].x, xv[2 * j], a0);
+                a1 = fma(v[j].y, xv[2 * j + 1], a1);
+            }
+        }
         for (; k + 4 <= w; k += 4) {
             const int2 ca = __ldg(c2 + 16 * k), cb = __ldg(c2 + 16 * k + 32);
             const double2 va = __ldg(v2 + 16 * k), vb = __ldg(v2 + 16 * k + 32);
@@ -103,6 +127,26 @@ struct SellF32Diff {
             const float2 *v2 = reinterpret_cast<const float2 *>(val + base) + lane;
             float a0 = 0.0f, a1 = 0.0f;
             int k = 0;
+            for (; k + 8 <= w; k += 8) {   // loads of 8 entries in flight together
+                int2 c[4];
+                float2 v[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    c[j] = __ldg(c2 + 16 * (k + 2 * j));
+                    v[j] = __ldg(v2 + 16 * (k + 2 * j));
+                }
+                float xv[8];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    xv[2 * j] = x[c[j].x];
+                    xv[2 * j + 1] = x[c[j].y];
+                }
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    a0 = fmaf(v[j].x, xv[2 * j] - xi, a0);
+                    a1 = fmaf(v[j].y, xv[2 * j + 1] - xi, a1);
+                }
+            }
             for (; k + 4 <= w; k += 4) {
                 const int2 ca = __ldg(c2 + 16 * k), cb = __ldg(c2 + 16 * k + 32);
                 const float2 va = __ldg(v2 + 16 * k), vb = __ldg(v2 + 16 * k + 32);

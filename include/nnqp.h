@@ -300,7 +300,8 @@ typedef struct nn_server nn_server;
 typedef struct {
     int max_inflight;       /* concurrent requests on the device (default 8) */
     int queue_capacity;     /* waiting requests before submit returns BUSY (default 100000) */
-    int sm_share_blocks;    /* persistent blocks granted per large request (0 = auto) */
+    int sm_share_blocks;    /* most persistent blocks of one request (0 = the whole co-resident
+                               grid: large requests run alone, small ones side by side) */
     nn_solve_opts solve;    /* per-request solver options */
 } nn_serve_opts;
 

@@ -153,6 +153,7 @@ static nn_status run_batch(int count, nn_system *const *systems, double *const *
     if (const char *e = getenv("NNQP_BATCH_CG_VARIANT")) ctl.cg_variant = atoi(e);
     if (const char *e = getenv("NNQP_CG_BOUND_STOP")) ctl.cg_bound_stop = atoi(e);
     if (const char *e = getenv("NNQP_GP_MAX")) ctl.gp_max = atoi(e);
+    if (const char *e = getenv("NNQP_ETA1")) ctl.eta1 = atof(e);
     if (const char *e = getenv("NNQP_ETA2")) ctl.eta2 = atof(e);
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);

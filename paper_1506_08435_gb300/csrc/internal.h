@@ -45,6 +45,16 @@ struct SellMat {
 };
 
 // Device allocations owned by one object, released together.
+// The library's stream-ordered memory pool on the current device.  Unlike
+// the device's default pool it never makes one stream wait for another to
+// reuse freed memory (no internal dependencies), so solves running on
+// different streams (serving workers, user streams) stay concurrent; freed
+// memory stays cached in the pool up to a release threshold.
+cudaMemPool_t device_pool();
+
+// Stream-ordered allocation from device_pool().
+cudaError_t pool_alloc(void **p, size_t bytes, cudaStream_t st);
+
 struct DevArena {
     std::vector<void *> ptrs;
     size_t bytes = 0;
@@ -53,7 +63,7 @@ struct DevArena {
         *out = nullptr;
         if (count == 0) count = 1;
         void *p = nullptr;
-        cudaError_t e = cudaMallocAsync(&p, count * sizeof(T), st);
+        cudaError_t e = pool_alloc(&p, count * sizeof(T), st);
         if (e != cudaSuccess) {
             set_error("device allocation of %zu bytes failed: %s", count * sizeof(T), cudaGetErrorString(e));
             return e == cudaErrorMemoryAllocation ? NN_ERR_OOM : NN_ERR_CUDA;

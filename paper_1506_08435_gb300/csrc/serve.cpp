@@ -3,13 +3,16 @@
 // Requests are queued by nn_serve_submit (host arrays copied at once).  A
 // scheduler thread admits the oldest queued request when (a) a worker slot
 // is free, (b) its device-memory estimate fits in the HBM budget next to the
-// requests already resident, and (c) its persistent solve grid fits in the
-// SM-block budget next to the grids of the requests already running.  Each
-// worker owns a CUDA stream: it assembles the request's system, solves it in
-// one persistent launch and copies the solution back, so the device work of
-// different requests overlaps.  Because the grids of all running solves fit
-// on the device together, no solve ever waits for blocks that cannot
-// become resident.
+// requests already resident, and (c) its thread blocks fit in the SM-block
+// budget next to those of the requests already running.  Each worker owns a
+// CUDA stream: it assembles the request's system, solves it in one launch
+// and copies the solution back, so the device work of different requests
+// overlaps.  Every request is solved by a persistent cooperative grid of at
+// most a fixed share of the device (fewer blocks for small requests).
+// Because the blocks of all running solves fit on the device together, no
+// solve ever waits for blocks that cannot become resident.  (One thread-block
+// cluster per request was measured too: on 8-16 SMs a request's FP64 passes
+// take 3-10x longer than on its grid share, and small requests gain nothing.)
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -103,7 +106,7 @@ void worker_loop(Server *sv) {
         nn_status stt = assemble_impl(&r->p, &ao, st, &s);
         double *dc = nullptr;
         if (stt == NN_OK) {
-            if (cudaMallocAsync(&dc, sizeof(double) * r->N, st) != cudaSuccess) stt = NN_ERR_OOM;
+            if (pool_alloc((void **)&dc, sizeof(double) * r->N, st) != cudaSuccess) stt = NN_ERR_OOM;
         }
         if (stt == NN_OK) {
             cudaMemsetAsync(dc, 0, sizeof(double) * r->N, st);
@@ -261,10 +264,13 @@ nn_status nn_serve_submit(nn_server *h, const nn_problem *p, uint64_t *request_i
         set_error("nn_serve_submit: the request alone (%zu bytes) exceeds the budget", r->bytes);
         return NN_ERR_INVALID_ARG;
     }
-    // persistent grid: a fixed share, or one block per 8 slices, within the share
+    // persistent grid: one block per 8 slices, at most the share.  By default
+    // the share is the whole co-resident grid: a large request then runs
+    // alone at full speed (bandwidth- and FP64-bound solves gain nothing from
+    // sharing the device, and co-resident blocks of other grids slow their
+    // barriers), while small requests, whose grids are small, run side by side.
     const int64_t slices = (r->N + 31) / 32;
-    const int share = sv->opts.sm_share_blocks > 0 ? sv->opts.sm_share_blocks
-                                                   : std::max(1, sv->capacity / sv->opts.max_inflight);
+    const int share = sv->opts.sm_share_blocks > 0 ? sv->opts.sm_share_blocks : sv->capacity;
     r->blocks = (int)std::max<int64_t>(1, std::min<int64_t>((slices + 7) / 8, std::min(share, sv->capacity)));
     const int ncoef = p->coef_kind == NN_COEF_TENSOR ? (dim == 2 ? 3 : 6) : dim;
     r->coef.assign(p->coef, p->coef + (size_t)r->E * ncoef);

@@ -39,7 +39,7 @@ import nn_inputs as I  # noqa: E402
 
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM = 6800.0
-FP64_FMA_PEAK_TFLOPS = 1.21   # measured register-only FMA chains on this machine's GB300
+FP64_PIPE_PEAK_GFLOPS = 152 * 2 * 2 * 2.07   # SMs x DFMA per clock (ncu unit count) x flop x GHz
 
 
 def peaks():
@@ -541,6 +541,13 @@ def main():
             "max_kkt_rel": float(max(i["kkt_rel"] for i in infos)),
             "statuses_ok": all(i["status"] == 0 for i in infos),
             "spmv_per_step": sum(i["spmv"] for i in infos) / args.steps}
+    # the FP64 pipe as a second bound: algorithmic FP64 operations of the dominant
+    # kernel per launch / its time, against 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
+    fl64 = sum(i.get("flops64_algo", 0.0) for i in infos) / args.steps
+    if fl64 > 0:
+        ach = fl64 / (kern_ms / 1e3) / 1e9
+        line["fp64_pipe"] = {"achieved": ach, "peak": FP64_PIPE_PEAK_GFLOPS, "unit": "GFLOP/s",
+                             "frac": ach / FP64_PIPE_PEAK_GFLOPS, "flops_per_launch": fl64}
     if r["e2e"] is not None:
         e2e_ms = max_over_ranks(dist, sum(r["e2e"]))
         line["e2e"] = {"value": r["units_per_step"] * len(r["e2e"]) * ws / (e2e_ms / 1e3), "unit": r["unit"],

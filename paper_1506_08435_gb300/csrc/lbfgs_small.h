@@ -25,14 +25,19 @@ constexpr int kLbfgsMax = 16;
 // singular (then the caller falls back to a gradient step).
 NN_HD inline bool lbfgs_coefficients(int k, const double *SY, const double *YY, const double *u,
                                      const double *v, double gamma, double *cs, double *cy) {
-    double t[kLbfgsMax], w[kLbfgsMax];
+    double t[kLbfgsMax], w[kLbfgsMax], rinv[kLbfgsMax];
+    // reciprocals of R's diagonal first: k independent divisions instead of
+    // one division on every step of both substitution chains
+    for (int i = 0; i < k; ++i) {
+        const double rii = SY[i * kLbfgsMax + i];
+        if (!(rii > 0.0)) return false;
+        rinv[i] = 1.0 / rii;
+    }
     // back substitution R t = u, R upper triangular with R_ij = SY[i][j]
     for (int i = k - 1; i >= 0; --i) {
         double s = u[i];
         for (int j = i + 1; j < k; ++j) s -= SY[i * kLbfgsMax + j] * t[j];
-        const double rii = SY[i * kLbfgsMax + i];
-        if (!(rii > 0.0)) return false;
-        t[i] = s / rii;
+        t[i] = s * rinv[i];
     }
     // w = (D + gamma Y^T Y) t - gamma v
     for (int i = 0; i < k; ++i) {
@@ -44,7 +49,7 @@ NN_HD inline bool lbfgs_coefficients(int k, const double *SY, const double *YY, 
     for (int i = 0; i < k; ++i) {
         double s = w[i];
         for (int j = 0; j < i; ++j) s -= SY[j * kLbfgsMax + i] * cs[j];
-        cs[i] = s / SY[i * kLbfgsMax + i];
+        cs[i] = s * rinv[i];
     }
     for (int i = 0; i < k; ++i) cy[i] = -gamma * t[i];
     return true;

@@ -233,14 +233,42 @@ struct GridTeam {
             for (int k = lane; k < K; k += 32) P[(size_t)k * nblocks + blockIdx.x] = sm->bcast[k];
         }
         if (!sync()) return false;
-        // warp w sums the per-block partials of entries k = w, w + nw, ...;
-        // the loads of different entries are in flight together
-        for (int k = warp; k < K; k += nw) {
-            double u = 0.0;
-            for (int b = lane; b < nblocks; b += 32) u += __ldcg(P + (size_t)k * nblocks + b);
+        if (K <= nw) {
+            // warp k sums the per-block partials of entry k; the loads of
+            // different entries are in flight together
+            for (int k = warp; k < K; k += nw) {
+                double u = 0.0;
+                for (int b = lane; b < nblocks; b += 32) u += __ldcg(P + (size_t)k * nblocks + b);
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) u += __shfl_xor_sync(0xffffffffu, u, o);
-            if (lane == 0) sm->bcast[k] = u;
+                for (int o = 16; o > 0; o >>= 1) u += __shfl_xor_sync(0xffffffffu, u, o);
+                if (lane == 0) sm->bcast[k] = u;
+            }
+        } else {
+            // wide reductions: CH threads per entry, each summing every CH-th
+            // partial in four independent chains (short FP64 dependency
+            // chains), then one thread per entry adds the CH chunk sums in order
+            const int CH = (int)blockDim.x / K < kMaxWarps ? (int)blockDim.x / K : kMaxWarps;
+            const int t = threadIdx.x;
+            if (t < K * CH) {
+                const int k = t / CH, c = t - k * CH;
+                const double *Pk = P + (size_t)k * nblocks;
+                double u0 = 0.0, u1 = 0.0, u2 = 0.0, u3 = 0.0;
+                int b = c;
+                for (; b + 3 * CH < nblocks; b += 4 * CH) {
+                    u0 += __ldcg(Pk + b);
+                    u1 += __ldcg(Pk + b + CH);
+                    u2 += __ldcg(Pk + b + 2 * CH);
+                    u3 += __ldcg(Pk + b + 3 * CH);
+                }
+                for (; b < nblocks; b += CH) u0 += __ldcg(Pk + b);
+                sm->warp[c][k] = (u0 + u1) + (u2 + u3);
+            }
+            __syncthreads();
+            if (t < K) {
+                double u = 0.0;
+                for (int c = 0; c < CH; ++c) u += sm->warp[c][t];
+                sm->bcast[t] = u;
+            }
         }
         __syncthreads();
 #pragma unroll

@@ -23,6 +23,26 @@ __host__ __device__ __forceinline__ int64_t sell_idx(int64_t base, int k, int la
     return base + 64 * (int64_t)(k >> 1) + 2 * lane + (k & 1);
 }
 
+// Matrix loads.  An operator larger than about half of L2 streams through it
+// once per product: its loads are marked evict-first (cache-streaming), so
+// that the gathered vector stays in L2.  A smaller operator is reused from
+// L2 by every product and is loaded normally.
+template <typename T>
+__device__ __forceinline__ T mat_load(const T *p, bool stream) {
+    return stream ? __ldcs(p) : __ldg(p);
+}
+
+// Asks L2 for the column and value bytes [b0, b1) of a slice ahead of use:
+// every lane of the warp prefetches its share of the 128-byte lines, so a
+// warp has the next slice's operator in flight while it works on this one.
+__device__ __forceinline__ void prefetch_slice(const void *col, const void *val, int vbytes, int64_t b0, int64_t b1,
+                                               int lane) {
+    const char *c = (const char *)col + b0 * 4, *v = (const char *)val + b0 * vbytes;
+    const int cl = (int)(((b1 - b0) * 4 + 127) >> 7), vl = (int)(((b1 - b0) * vbytes + 127) >> 7);
+    for (int l = lane; l < cl; l += 32) asm volatile("prefetch.global.L2 [%0];" ::"l"(c + 128 * l));
+    for (int l = lane; l < vl; l += 32) asm volatile("prefetch.global.L2 [%0];" ::"l"(v + 128 * l));
+}
+
 // SELL-32, FP64 values; off-diagonals in slices, diagonal separate:
 //   y_i = d_i x_i + sum_k v_ik x_{c_ik}
 struct SellF64 {
@@ -31,6 +51,7 @@ struct SellF64 {
     const int32_t *__restrict__ col;
     const double *__restrict__ val;
     const double *__restrict__ diag;
+    bool stream = false;          // operator larger than L2: streaming loads + slice prefetch
 
     template <typename VX>
     __device__ __forceinline__ double row(int64_t s, int lane, int64_t base, int w, const VX *x) const {
@@ -47,8 +68,8 @@ struct SellF64 {
             double2 v[4];
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                c[j] = __ldg(c2 + 16 * (k + 2 * j));
-                v[j] = __ldg(v2 + 16 * (k + 2 * j));
+                c[j] = mat_load(c2 + 16 * (k + 2 * j), stream);
+                v[j] = mat_load(v2 + 16 * (k + 2 * j), stream);
             }
             double xv[8];
 #pragma unroll
@@ -63,16 +84,16 @@ struct SellF64 {
             }
         }
         for (; k + 4 <= w; k += 4) {
-            const int2 ca = __ldg(c2 + 16 * k), cb = __ldg(c2 + 16 * k + 32);
-            const double2 va = __ldg(v2 + 16 * k), vb = __ldg(v2 + 16 * k + 32);
+            const int2 ca = mat_load(c2 + 16 * k, stream), cb = mat_load(c2 + 16 * k + 32, stream);
+            const double2 va = mat_load(v2 + 16 * k, stream), vb = mat_load(v2 + 16 * k + 32, stream);
             a0 = fma(va.x, (double)x[ca.x], a0);
             a1 = fma(va.y, (double)x[ca.y], a1);
             a0 = fma(vb.x, (double)x[cb.x], a0);
             a1 = fma(vb.y, (double)x[cb.y], a1);
         }
         if (k < w) {
-            const int2 ca = __ldg(c2 + 16 * k);
-            const double2 va = __ldg(v2 + 16 * k);
+            const int2 ca = mat_load(c2 + 16 * k, stream);
+            const double2 va = mat_load(v2 + 16 * k, stream);
             a0 = fma(va.x, (double)x[ca.x], a0);
             a1 = fma(va.y, (double)x[ca.y], a1);
         }
@@ -85,6 +106,7 @@ struct SellF64 {
         for (int64_t s = R.s0 + (threadIdx.x >> 5); s < R.s1; s += nw) {
             const int64_t base = __ldg(sptr + s);
             const int w = (int)((__ldg(sptr + s + 1) - base) >> 5);
+            if (stream && s + nw < R.s1) prefetch_slice(col, val, 8, __ldg(sptr + s + nw), __ldg(sptr + s + nw + 1), lane);
             const int64_t i = s * 32 + lane;
             const double acc = row(s, lane, base, w, x);
             if (i < n) epi(i, fma(__ldg(diag + i), x[i], acc));
@@ -114,6 +136,7 @@ struct SellF32Diff {
     const int32_t *__restrict__ col;
     const float *__restrict__ val;
     const float *__restrict__ rsum;
+    bool stream = false;          // operator larger than L2: streaming loads + slice prefetch
 
     template <class Epi>
     __device__ __forceinline__ void apply(const Rows &R, const float *x, Epi &&epi) const {
@@ -121,6 +144,7 @@ struct SellF32Diff {
         for (int64_t s = R.s0 + (threadIdx.x >> 5); s < R.s1; s += nw) {
             const int64_t base = __ldg(sptr + s);
             const int w = (int)((__ldg(sptr + s + 1) - base) >> 5);
+            if (stream && s + nw < R.s1) prefetch_slice(col, val, 4, __ldg(sptr + s + nw), __ldg(sptr + s + nw + 1), lane);
             const int64_t i = s * 32 + lane;
             const float xi = i < n ? x[i] : 0.0f;
             const int2 *c2 = reinterpret_cast<const int2 *>(col + base) + lane;
@@ -132,8 +156,8 @@ struct SellF32Diff {
                 float2 v[4];
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
-                    c[j] = __ldg(c2 + 16 * (k + 2 * j));
-                    v[j] = __ldg(v2 + 16 * (k + 2 * j));
+                    c[j] = mat_load(c2 + 16 * (k + 2 * j), stream);
+                    v[j] = mat_load(v2 + 16 * (k + 2 * j), stream);
                 }
                 float xv[8];
 #pragma unroll
@@ -148,16 +172,16 @@ struct SellF32Diff {
                 }
             }
             for (; k + 4 <= w; k += 4) {
-                const int2 ca = __ldg(c2 + 16 * k), cb = __ldg(c2 + 16 * k + 32);
-                const float2 va = __ldg(v2 + 16 * k), vb = __ldg(v2 + 16 * k + 32);
+                const int2 ca = mat_load(c2 + 16 * k, stream), cb = mat_load(c2 + 16 * k + 32, stream);
+                const float2 va = mat_load(v2 + 16 * k, stream), vb = mat_load(v2 + 16 * k + 32, stream);
                 a0 = fmaf(va.x, x[ca.x] - xi, a0);
                 a1 = fmaf(va.y, x[ca.y] - xi, a1);
                 a0 = fmaf(vb.x, x[cb.x] - xi, a0);
                 a1 = fmaf(vb.y, x[cb.y] - xi, a1);
             }
             if (k < w) {
-                const int2 ca = __ldg(c2 + 16 * k);
-                const float2 va = __ldg(v2 + 16 * k);
+                const int2 ca = mat_load(c2 + 16 * k, stream);
+                const float2 va = mat_load(v2 + 16 * k, stream);
                 a0 = fmaf(va.x, x[ca.x] - xi, a0);
                 a1 = fmaf(va.y, x[ca.y] - xi, a1);
             }

@@ -133,14 +133,19 @@ __global__ void __launch_bounds__(256) k_spmv32(SellF32Diff A, const float *x, d
 
 namespace {
 
+// Operators larger than this stream through L2 (evict-first loads, slice prefetch).
+constexpr double kStreamBytes = 48.0 * (1 << 20);
+
 SellF64 view64(const nn_system *s) {
-    return SellF64{s->NF, s->A64.nslices, s->A64.sptr, s->A64.col, s->A64.val, s->diag64};
+    return SellF64{s->NF, s->A64.nslices, s->A64.sptr, s->A64.col, s->A64.val, s->diag64,
+                   (double)s->nnzF * 12.0 > kStreamBytes};
 }
 SellF64 viewM(const nn_system *s) {
     return SellF64{s->NF, s->M64.nslices, s->M64.sptr, s->M64.col, s->M64.val, s->mdiag64};
 }
 SellF32Diff view32(const nn_system *s) {
-    return SellF32Diff{s->NF, s->A32.nslices, s->A32.sptr, s->A32.col, s->A32.val, s->rsum32};
+    return SellF32Diff{s->NF, s->A32.nslices, s->A32.sptr, s->A32.col, s->A32.val, s->rsum32,
+                       (double)s->nnzF * 8.0 > kStreamBytes};
 }
 CsrF64 viewcsr(const nn_system *s) { return CsrF64{s->NF, s->A64.nslices, s->arow, s->acol, s->aval}; }
 

@@ -276,7 +276,7 @@ def run_transient(P, torch, args, rank):
                 config={"workload": "transient3d_n40_dt0.01_50steps", "nodes": spec.n_nodes,
                         "tets": spec.n_elems, "qp_per_step": nsteps, "rtol": args.rtol,
                         "l2": "flushed between steps (256 MB write)", "solver": args.solver,
-                        "precision": args.precision, "first_iterate": "projected 2c^n - c^(n-1)"},
+                        "precision": args.precision, "first_iterate": "projected 3c^n - 3c^(n-1) + c^(n-2)"},
                 dtype="f32+f64" if mixed else "f64", unit="QP solves/s", metric="QP solves/s")
 
 

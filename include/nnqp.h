@@ -178,9 +178,11 @@ typedef struct {
     int grid_blocks;     /* persistent grid size; 0 = chosen from the size */
     double wait_timeout_s; /* bound on every device-side wait (default 5 s) */
     double inner_rtol;   /* mixed: relative tolerance of each inner solve (default 1e-4) */
-    int extrapolate;     /* transient: 1 (default) starts the QP of step n+1 from the box
-                            projection of 2 c^(n) - c^(n-1) (the QP and its solution are
-                            unchanged, only the first iterate moves); 0 starts from c^(n) */
+    int extrapolate;     /* transient: first iterate of the QP of step n+1 (the QP and its
+                            solution are unchanged, only the first iterate moves):
+                            0 = c^(n); 1 = box projection of 2 c^(n) - c^(n-1);
+                            2 (default) = box projection of 3 c^(n) - 3 c^(n-1) + c^(n-2)
+                            (measured on the 40^3 run: 6,853 / 5,817 / 5,356 products) */
 } nn_solve_opts;
 
 void nn_solve_opts_default(nn_solve_opts *o);

@@ -55,9 +55,12 @@ struct GridArgs {
     double *S, *Y;          // (m+1) slots of n doubles each
     int m;
     double h0;
-    // transient: initial iterate of step n+1 is P(2 c^(n) - c^(n-1)) when set
+    // transient: initial iterate of step n+1 (option extrapolate): 1 = the box
+    // projection of the linear extrapolation 2 c^(n) - c^(n-1), 2 = of the
+    // quadratic one 3 c^(n) - 3 c^(n-1) + c^(n-2); 0 = c^(n)
     int predict;
     double *xprev;          // [n] c^(n-1) at the free nodes
+    double *xprev2;         // [n] c^(n-2) (quadratic extrapolation)
     uint8_t *fmask;         // [n] face mask of the CG phases
 };
 
@@ -69,7 +72,13 @@ __device__ void transient_predict(const Rows &R, const GridArgs &a, double *x, i
     if (!a.predict) return;
     R.each([&](int64_t i) {
         const double xn = x[i];
-        if (step > 0) x[i] = clampv(xn + (xn - a.xprev[i]), a.lo, a.hi);
+        const double x1 = a.xprev[i];
+        if (a.predict == 2 && step > 1) {
+            x[i] = clampv(3.0 * (xn - x1) + a.xprev2[i], a.lo, a.hi);
+        } else if (step > 0) {
+            x[i] = clampv(xn + (xn - x1), a.lo, a.hi);
+        }
+        if (a.predict == 2) a.xprev2[i] = x1;
         a.xprev[i] = xn;
     });
 }

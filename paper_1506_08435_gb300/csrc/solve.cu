@@ -305,6 +305,7 @@ nn_status run_grid(nn_system *s, const nn_solve_opts *o, int mode, int nsteps, c
     }
     a.predict = o->extrapolate;
     if (mode_transient(mode) && a.predict) NN_TRY(S.a.alloc(&a.xprev, n, st));
+    if (mode_transient(mode) && a.predict == 2) NN_TRY(S.a.alloc(&a.xprev2, n, st));
     // Grid: one slice per warp at least.  Systems that a grid of one block
     // per SM covers in a few slices per warp run one block per SM (fewer
     // barrier arrivals) of 512 threads (one slice per warp: all loads of a

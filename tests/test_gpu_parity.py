@@ -256,7 +256,7 @@ def test_not_converged_returns_feasible_iterate():
 
 # ------------------------------------------------------------------ transient
 
-@pytest.mark.parametrize("extrapolate,prec", [(0, "fp64"), (1, "fp64"), (1, "mixed")])
+@pytest.mark.parametrize("extrapolate,prec", [(0, "fp64"), (1, "fp64"), (2, "fp64"), (1, "mixed")])
 def test_transient_small_matches_oracle_trajectory(extrapolate, prec):
     """Either first iterate (c^(n), or the projected extrapolation
     2 c^(n) - c^(n-1)) and either precision (FP64, or FP32 inner solves

@@ -278,7 +278,12 @@ nn_status run_grid(nn_system *s, const nn_solve_opts *o, int mode, int nsteps, c
     a.ctl.eta1 = 0.1;
     a.ctl.eta2 = 1e-3;
     a.ctl.mu = 1e-4;
-    a.ctl.cg_variant = n < (1 << 20) ? 1 : 0;
+    // CG form: the pipelined one (one barrier per iteration) where barrier
+    // latency bounds the solve; the textbook one on large systems, where the
+    // passes stream HBM and the pipelined form's extra vector streams cost
+    // more than its saved barriers (measured: 40^3 transient 71.6 -> 64.4 ms,
+    // 50^2 steady 4.5 -> 4.0 ms; 150^3 steady 4.12 -> 4.31 s)
+    a.ctl.cg_variant = n < (1 << 20) ? 2 : 0;
     a.ctl.cg_bound_stop = 0;
     if (const char *e = getenv("NNQP_CG_VARIANT")) a.ctl.cg_variant = atoi(e);
     if (const char *e = getenv("NNQP_CG_BOUND_STOP")) a.ctl.cg_bound_stop = atoi(e);

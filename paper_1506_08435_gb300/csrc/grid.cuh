@@ -131,13 +131,40 @@ __device__ bool step_outputs(Team &T, const Rows &R, const GridArgs &a, const do
 // TPB threads per block: 256 (several blocks per SM on large systems) or 512
 // (one block per SM on mid-size systems: one slice per warp, so the loads of
 // a pass are all in flight at once).
+// FMT: 0 = SELL, 1 = CSR (FP64), 2 = SELL with the block's slices of the
+// operator that the inner products use (FP64 A, or FP32 A in the mixed
+// modes) held in shared memory for the whole launch: staged once, then every
+// product reads its columns and values on chip and only gathers x from L2
+// (mid-size systems, whose slices per block fit in shared memory).
 template <int FMT, int MODE, int CGV, int TPB>
 __global__ void __launch_bounds__(TPB, TPB >= 512 ? 1 : mode_min_blocks(MODE)) k_solve_grid(GridArgs a) {
     __shared__ RedSmem sm;
+    extern __shared__ __align__(16) unsigned char op_smem[];
     GridTeam T{a.bar, a.partials, (int)gridDim.x + a.bar_extra, a.timeout_ns, 0, 0, &sm};
     const Rows R = rows_of_block(a.n, a.nslices, blockIdx.x, gridDim.x);
     double *x = a.v64[0];
     R.each([&](int64_t i) { x[i] = a.c_in[a.free_node[i]]; });
+    SellF64Local Aloc{};
+    SellF32DiffLocal A32loc{};
+    if constexpr (FMT == 2) {
+        // stage entries [e0, e1) of this block's slices: columns, then values
+        constexpr bool MIX = mode_mixed(MODE);
+        const int64_t e0 = a.A.sptr[R.s0], e1 = a.A.sptr[R.s1];
+        const int64_t ne = e1 - e0;   // a multiple of 64 (32-row slices, even widths)
+        int32_t *scol = reinterpret_cast<int32_t *>(op_smem);
+        unsigned char *sv = op_smem + ne * 4;
+        const int4 *gc = reinterpret_cast<const int4 *>(a.A.col + e0);
+        for (int64_t q = threadIdx.x; q < ne / 4; q += blockDim.x) reinterpret_cast<int4 *>(scol)[q] = __ldg(gc + q);
+        const int vbytes = MIX ? 4 : 8;
+        const int4 *gv = MIX ? reinterpret_cast<const int4 *>(a.A32.val + e0) : reinterpret_cast<const int4 *>(a.A.val + e0);
+        for (int64_t q = threadIdx.x; q < ne * vbytes / 16; q += blockDim.x) reinterpret_cast<int4 *>(sv)[q] = __ldg(gv + q);
+        if constexpr (MIX)
+            A32loc = SellF32DiffLocal{a.A32.n, a.A32.nslices, a.A32.sptr, scol, reinterpret_cast<const float *>(sv),
+                                      a.A32.rsum, false, e0};
+        else
+            Aloc = SellF64Local{a.A.n, a.A.nslices, a.A.sptr, scol, reinterpret_cast<const double *>(sv), a.A.diag,
+                                false, e0};
+    }
     if (!T.sync()) return;
     const int nsteps = mode_transient(MODE) ? a.nsteps : 1;
     for (int step = 0; step < nsteps; ++step) {
@@ -158,9 +185,14 @@ __global__ void __launch_bounds__(TPB, TPB >= 512 ? 1 : mode_min_blocks(MODE)) k
             GpcgVecs<double> v64{x, a.v64[1], a.v64[2], a.v64[3], a.v64[4], a.v64[5],
                                  a.v64[6], a.v64[7], a.v64[8], b, a.dinv64, a.fmask, a.v64[10]};
             MixedStats ms;
-            status = mixed_solve<CGV, true>(T, R, a.A, a.A32, a.lo, a.hi, b, x, v, a.v32[9], a.v32[10], a.v32[11], v64,
-                                 a.rtol * den, a.inner_rtol, a.max_ref, a.ctl.max_spmv,
-                                 inner_product_cap(a.n), a.ctl, a.ctl, ms);
+            if constexpr (FMT == 2)
+                status = mixed_solve<CGV, true>(T, R, a.A, A32loc, a.lo, a.hi, b, x, v, a.v32[9], a.v32[10],
+                                                 a.v32[11], v64, a.rtol * den, a.inner_rtol, a.max_ref,
+                                                 a.ctl.max_spmv, inner_product_cap(a.n), a.ctl, a.ctl, ms);
+            else
+                status = mixed_solve<CGV, true>(T, R, a.A, a.A32, a.lo, a.hi, b, x, v, a.v32[9], a.v32[10],
+                                                 a.v32[11], v64, a.rtol * den, a.inner_rtol, a.max_ref,
+                                                 a.ctl.max_spmv, inner_product_cap(a.n), a.ctl, a.ctl, ms);
             if (status == ST_TIMEOUT) return;
             cnt[1] += ms.spmv64;
             cnt[2] += ms.spmv32;
@@ -180,10 +212,13 @@ __global__ void __launch_bounds__(TPB, TPB >= 512 ? 1 : mode_min_blocks(MODE)) k
             c.tol = a.rtol * den;
             c.face_tol = 0.5 * c.tol;
             GpcgStats gs;
-            if (FMT == 0)
-                status = gpcg_solve<GridTeam, SellF64, double, CGV>(T, R, a.A, Bounds<double>{a.lo, a.hi, nullptr, nullptr}, v, c, gs);
+            const Bounds<double> B{a.lo, a.hi, nullptr, nullptr};
+            if constexpr (FMT == 0)
+                status = gpcg_solve<GridTeam, SellF64, double, CGV>(T, R, a.A, B, v, c, gs);
+            else if constexpr (FMT == 2)
+                status = gpcg_solve<GridTeam, SellF64Local, double, CGV>(T, R, Aloc, B, v, c, gs);
             else
-                status = gpcg_solve<GridTeam, CsrF64, double, CGV>(T, R, a.Acsr, Bounds<double>{a.lo, a.hi, nullptr, nullptr}, v, c, gs);
+                status = gpcg_solve<GridTeam, CsrF64, double, CGV>(T, R, a.Acsr, B, v, c, gs);
             if (status == ST_TIMEOUT) return;
             x = v.x;
             // keep the solution in slot 0 so that the next step starts there
@@ -205,9 +240,12 @@ __global__ void __launch_bounds__(TPB, TPB >= 512 ? 1 : mode_min_blocks(MODE)) k
 
 using GridKernel = void (*)(GridArgs);
 
-// Kernel of one mode for format fmt (NN_FMT_SELL / NN_FMT_CSR), CG variant
-// cgv (0, 1, 2) and threads per block tpb (256, 512); nullptr if that
-// combination is not built.
+// Internal format code of the shared-memory-resident SELL operator.
+constexpr int FMT_SELL_SMEM = 2;
+
+// Kernel of one mode for format fmt (NN_FMT_SELL / NN_FMT_CSR /
+// FMT_SELL_SMEM), CG variant cgv (0, 1, 2) and threads per block tpb (256,
+// 512); nullptr if that combination is not built.
 GridKernel grid_kernel_steady(int fmt, int cgv, int tpb);
 GridKernel grid_kernel_transient(int fmt, int cgv, int tpb);
 GridKernel grid_kernel_mixed(int fmt, int cgv, int tpb);

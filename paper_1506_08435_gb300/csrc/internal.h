@@ -106,6 +106,7 @@ struct nn_system {
     double *diag64 = nullptr;       // [NF]
     double *dinv64 = nullptr;       // [NF]
     nnqp::SellMat<float> A32;       // off-diagonals, FP32 (shares sptr/col with A64)
+    std::vector<int64_t> sptr_host; // host copy of A64.sptr, made on first use (grid sizing)
     float *rsum32 = nullptr;        // [NF] row sums of A over free columns
     float *dinv32 = nullptr;        // [NF] 1 / (rsum - sum of FP32 off-diagonals)
     nnqp::SellMat<double> M64;      // transient: off-diagonals of M_FF (shares sptr/col)

@@ -27,9 +27,14 @@ __host__ __device__ __forceinline__ int64_t sell_idx(int64_t base, int k, int la
 // once per product: its loads are marked evict-first (cache-streaming), so
 // that the gathered vector stays in L2.  A smaller operator is reused from
 // L2 by every product and is loaded normally.
-template <typename T>
+// LOCAL operators hold a block's slices in shared memory (staged once per
+// launch) and are read with ordinary loads.
+template <bool LOCAL, typename T>
 __device__ __forceinline__ T mat_load(const T *p, bool stream) {
-    return stream ? __ldcs(p) : __ldg(p);
+    if constexpr (LOCAL)
+        return *p;
+    else
+        return stream ? __ldcs(p) : __ldg(p);
 }
 
 // Asks L2 for the column and value bytes [b0, b1) of a slice ahead of use:
@@ -45,18 +50,22 @@ __device__ __forceinline__ void prefetch_slice(const void *col, const void *val,
 
 // SELL-32, FP64 values; off-diagonals in slices, diagonal separate:
 //   y_i = d_i x_i + sum_k v_ik x_{c_ik}
-struct SellF64 {
+// LOCAL: col/val hold only the entries [e0, ...) of the calling block's
+// slices, in shared memory; entry e of the operator is col[e - e0].
+template <bool LOCAL>
+struct SellF64X {
     int64_t n, nslices;
     const int64_t *__restrict__ sptr;
     const int32_t *__restrict__ col;
     const double *__restrict__ val;
     const double *__restrict__ diag;
     bool stream = false;          // operator larger than L2: streaming loads + slice prefetch
+    int64_t e0 = 0;               // first entry held by col/val (LOCAL)
 
     template <typename VX>
     __device__ __forceinline__ double row(int64_t s, int lane, int64_t base, int w, const VX *x) const {
-        const int2 *c2 = reinterpret_cast<const int2 *>(col + base) + lane;
-        const double2 *v2 = reinterpret_cast<const double2 *>(val + base) + lane;
+        const int2 *c2 = reinterpret_cast<const int2 *>(col + (base - e0)) + lane;
+        const double2 *v2 = reinterpret_cast<const double2 *>(val + (base - e0)) + lane;
         double a0 = 0.0, a1 = 0.0;
         int k = 0;
         // 8 entries per step: every column/value load of the step is issued
@@ -68,8 +77,8 @@ struct SellF64 {
             double2 v[4];
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                c[j] = mat_load(c2 + 16 * (k + 2 * j), stream);
-                v[j] = mat_load(v2 + 16 * (k + 2 * j), stream);
+                c[j] = mat_load<LOCAL>(c2 + 16 * (k + 2 * j), stream);
+                v[j] = mat_load<LOCAL>(v2 + 16 * (k + 2 * j), stream);
             }
             double xv[8];
 #pragma unroll
@@ -84,16 +93,16 @@ struct SellF64 {
             }
         }
         for (; k + 4 <= w; k += 4) {
-            const int2 ca = mat_load(c2 + 16 * k, stream), cb = mat_load(c2 + 16 * k + 32, stream);
-            const double2 va = mat_load(v2 + 16 * k, stream), vb = mat_load(v2 + 16 * k + 32, stream);
+            const int2 ca = mat_load<LOCAL>(c2 + 16 * k, stream), cb = mat_load<LOCAL>(c2 + 16 * k + 32, stream);
+            const double2 va = mat_load<LOCAL>(v2 + 16 * k, stream), vb = mat_load<LOCAL>(v2 + 16 * k + 32, stream);
             a0 = fma(va.x, (double)x[ca.x], a0);
             a1 = fma(va.y, (double)x[ca.y], a1);
             a0 = fma(vb.x, (double)x[cb.x], a0);
             a1 = fma(vb.y, (double)x[cb.y], a1);
         }
         if (k < w) {
-            const int2 ca = mat_load(c2 + 16 * k, stream);
-            const double2 va = mat_load(v2 + 16 * k, stream);
+            const int2 ca = mat_load<LOCAL>(c2 + 16 * k, stream);
+            const double2 va = mat_load<LOCAL>(v2 + 16 * k, stream);
             a0 = fma(va.x, (double)x[ca.x], a0);
             a1 = fma(va.y, (double)x[ca.y], a1);
         }
@@ -106,7 +115,7 @@ struct SellF64 {
         for (int64_t s = R.s0 + (threadIdx.x >> 5); s < R.s1; s += nw) {
             const int64_t base = __ldg(sptr + s);
             const int w = (int)((__ldg(sptr + s + 1) - base) >> 5);
-            if (stream && s + nw < R.s1) prefetch_slice(col, val, 8, __ldg(sptr + s + nw), __ldg(sptr + s + nw + 1), lane);
+            if (!LOCAL && stream && s + nw < R.s1) prefetch_slice(col, val, 8, __ldg(sptr + s + nw), __ldg(sptr + s + nw + 1), lane);
             const int64_t i = s * 32 + lane;
             const double acc = row(s, lane, base, w, x);
             if (i < n) epi(i, fma(__ldg(diag + i), x[i], acc));
@@ -120,23 +129,29 @@ struct SellF64 {
         const int64_t base = sptr[s];
         const int w = (int)((sptr[s + 1] - base) >> 5);
         double acc = 0.0;
-        for (int k = 0; k < w; ++k) acc = fma(val[sell_idx(base, k, lane)], x[col[sell_idx(base, k, lane)]], acc);
+        for (int k = 0; k < w; ++k)
+            acc = fma(val[sell_idx(base - e0, k, lane)], x[col[sell_idx(base - e0, k, lane)]], acc);
         return fma(diag[i], x[i], acc);
     }
 };
+
+using SellF64 = SellF64X<false>;
+using SellF64Local = SellF64X<true>;
 
 // SELL-32, FP32 values, FP32 vectors, in difference form:
 //   y_i = s_i x_i + sum_k v_ik (x_{c_ik} - x_i),   s_i = sum_j A_ij (row sum)
 // The implied diagonal is s_i - sum_k v_ik, so rounding the off-diagonals to
 // FP32 perturbs A by a matrix with zero row sums, and rounding in the
 // products scales with |x_j - x_i| instead of |x_j|.
-struct SellF32Diff {
+template <bool LOCAL>
+struct SellF32DiffX {
     int64_t n, nslices;
     const int64_t *__restrict__ sptr;
     const int32_t *__restrict__ col;
     const float *__restrict__ val;
     const float *__restrict__ rsum;
     bool stream = false;          // operator larger than L2: streaming loads + slice prefetch
+    int64_t e0 = 0;               // first entry held by col/val (LOCAL)
 
     template <class Epi>
     __device__ __forceinline__ void apply(const Rows &R, const float *x, Epi &&epi) const {
@@ -144,11 +159,11 @@ struct SellF32Diff {
         for (int64_t s = R.s0 + (threadIdx.x >> 5); s < R.s1; s += nw) {
             const int64_t base = __ldg(sptr + s);
             const int w = (int)((__ldg(sptr + s + 1) - base) >> 5);
-            if (stream && s + nw < R.s1) prefetch_slice(col, val, 4, __ldg(sptr + s + nw), __ldg(sptr + s + nw + 1), lane);
+            if (!LOCAL && stream && s + nw < R.s1) prefetch_slice(col, val, 4, __ldg(sptr + s + nw), __ldg(sptr + s + nw + 1), lane);
             const int64_t i = s * 32 + lane;
             const float xi = i < n ? x[i] : 0.0f;
-            const int2 *c2 = reinterpret_cast<const int2 *>(col + base) + lane;
-            const float2 *v2 = reinterpret_cast<const float2 *>(val + base) + lane;
+            const int2 *c2 = reinterpret_cast<const int2 *>(col + (base - e0)) + lane;
+            const float2 *v2 = reinterpret_cast<const float2 *>(val + (base - e0)) + lane;
             float a0 = 0.0f, a1 = 0.0f;
             int k = 0;
             for (; k + 8 <= w; k += 8) {   // loads of 8 entries in flight together
@@ -156,8 +171,8 @@ struct SellF32Diff {
                 float2 v[4];
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
-                    c[j] = mat_load(c2 + 16 * (k + 2 * j), stream);
-                    v[j] = mat_load(v2 + 16 * (k + 2 * j), stream);
+                    c[j] = mat_load<LOCAL>(c2 + 16 * (k + 2 * j), stream);
+                    v[j] = mat_load<LOCAL>(v2 + 16 * (k + 2 * j), stream);
                 }
                 float xv[8];
 #pragma unroll
@@ -172,16 +187,16 @@ struct SellF32Diff {
                 }
             }
             for (; k + 4 <= w; k += 4) {
-                const int2 ca = mat_load(c2 + 16 * k, stream), cb = mat_load(c2 + 16 * k + 32, stream);
-                const float2 va = mat_load(v2 + 16 * k, stream), vb = mat_load(v2 + 16 * k + 32, stream);
+                const int2 ca = mat_load<LOCAL>(c2 + 16 * k, stream), cb = mat_load<LOCAL>(c2 + 16 * k + 32, stream);
+                const float2 va = mat_load<LOCAL>(v2 + 16 * k, stream), vb = mat_load<LOCAL>(v2 + 16 * k + 32, stream);
                 a0 = fmaf(va.x, x[ca.x] - xi, a0);
                 a1 = fmaf(va.y, x[ca.y] - xi, a1);
                 a0 = fmaf(vb.x, x[cb.x] - xi, a0);
                 a1 = fmaf(vb.y, x[cb.y] - xi, a1);
             }
             if (k < w) {
-                const int2 ca = mat_load(c2 + 16 * k, stream);
-                const float2 va = mat_load(v2 + 16 * k, stream);
+                const int2 ca = mat_load<LOCAL>(c2 + 16 * k, stream);
+                const float2 va = mat_load<LOCAL>(v2 + 16 * k, stream);
                 a0 = fmaf(va.x, x[ca.x] - xi, a0);
                 a1 = fmaf(va.y, x[ca.y] - xi, a1);
             }
@@ -189,6 +204,9 @@ struct SellF32Diff {
         }
     }
 };
+
+using SellF32Diff = SellF32DiffX<false>;
+using SellF32DiffLocal = SellF32DiffX<true>;
 
 // CSR, FP64, one thread per row (rows taken in the same slice order as the
 // SELL operators so that every pass of a solve owns the same rows).

@@ -135,6 +135,8 @@ namespace {
 
 // Operators larger than this stream through L2 (evict-first loads, slice prefetch).
 constexpr double kStreamBytes = 48.0 * (1 << 20);
+// Most shared memory a block's staged operator slices may take.
+constexpr size_t kSmemOperatorBytes = 192 * 1024;
 
 SellF64 view64(const nn_system *s) {
     return SellF64{s->NF, s->A64.nslices, s->A64.sptr, s->A64.col, s->A64.val, s->diag64,
@@ -284,6 +286,7 @@ nn_status run_grid(nn_system *s, const nn_solve_opts *o, int mode, int nsteps, c
     // more than its saved barriers (measured: 40^3 transient 71.6 -> 64.4 ms,
     // 50^2 steady 4.5 -> 4.0 ms; 150^3 steady 4.12 -> 4.31 s)
     a.ctl.cg_variant = n < (1 << 20) ? 2 : 0;
+    if (fmt == NN_FMT_CSR && a.ctl.cg_variant == 2) a.ctl.cg_variant = 1;   // CSR kernels: forms 0 and 1
     a.ctl.cg_bound_stop = 0;
     if (const char *e = getenv("NNQP_CG_VARIANT")) a.ctl.cg_variant = atoi(e);
     if (const char *e = getenv("NNQP_CG_BOUND_STOP")) a.ctl.cg_bound_stop = atoi(e);
@@ -331,13 +334,45 @@ nn_status run_grid(nn_system *s, const nn_solve_opts *o, int mode, int nsteps, c
         set_error("CG variant %d is not available for this mode and format", a.ctl.cg_variant);
         return NN_ERR_INVALID_ARG;
     }
-    const int maxg = max_coresident(kern, tpb);
+    int maxg = max_coresident(kern, tpb);
     const int warps = tpb / 32;
     const int64_t by_rows = (slices + warps - 1) / warps;
     int want = (int)std::min<int64_t>(by_rows, slices <= (int64_t)4 * 8 * sms ? (int64_t)sms : (int64_t)maxg);
     want = std::min(want, maxg);
     if (o->grid_blocks > 0) want = std::min(o->grid_blocks, maxg);
     want = std::max(want, 1);
+    // Mid-size SELL solves keep each block's slices of the operator of the
+    // inner products in shared memory when they fit (one block per SM).
+    size_t dyn_smem = 0;
+    const char *sm_env = getenv("NNQP_SMEM_OP");
+    if (!lbfgs && fmt == NN_FMT_SELL && tpb == 512 && !(sm_env && sm_env[0] == '0')) {
+        if (s->sptr_host.empty()) {
+            s->sptr_host.resize((size_t)slices + 1);
+            NN_CUDA_TRY(cudaMemcpyAsync(s->sptr_host.data(), s->A64.sptr, sizeof(int64_t) * (slices + 1),
+                                        cudaMemcpyDeviceToHost, st));
+            NN_CUDA_TRY(cudaStreamSynchronize(st));
+        }
+        const int vbytes = mixed ? 4 : 8;
+        int64_t most = 0;
+        for (int b = 0; b < want; ++b) {
+            const Rows rb = rows_of_block(n, slices, b, want);
+            most = std::max(most, s->sptr_host[(size_t)rb.s1] - s->sptr_host[(size_t)rb.s0]);
+        }
+        const size_t bytes = (size_t)most * (4 + vbytes);
+        GridKernel ks = grid_kernel(mode, FMT_SELL_SMEM, a.ctl.cg_variant, tpb);
+        if (ks && bytes > 0 && bytes <= kSmemOperatorBytes &&
+            cudaFuncSetAttribute((const void *)ks, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) ==
+                cudaSuccess) {
+            int per = 0;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, ks, tpb, bytes);
+            if (per * sms >= want) {
+                kern = ks;
+                dyn_smem = bytes;
+                maxg = per * sms;
+            }
+        }
+        cudaGetLastError();   // a refused attribute leaves the plain kernel in use
+    }
     // NNQP_TEST_STALL_BARRIER=1 makes the grid barrier wait for one block
     // that does not exist, so every wait runs into its time limit: the test of
     // the bounded-wait path (no fault, the kernel returns TIMEOUT).
@@ -354,7 +389,7 @@ nn_status run_grid(nn_system *s, const nn_solve_opts *o, int mode, int nsteps, c
     NN_CUDA_TRY(cudaEventCreate(&e1));
     cudaEventRecord(e0, st);
     void *args[] = {&a};
-    cudaError_t le = cudaLaunchCooperativeKernel((void *)kern, dim3(want), dim3(tpb), args, 0, st);
+    cudaError_t le = cudaLaunchCooperativeKernel((void *)kern, dim3(want), dim3(tpb), args, dyn_smem, st);
     count_launch();
     if (le != cudaSuccess) {
         cudaEventDestroy(e0);

@@ -4,6 +4,14 @@
 namespace nnqp {
 
 GridKernel grid_kernel_mixed(int fmt, int cgv, int tpb) {
+    if (fmt == FMT_SELL_SMEM) {
+        if (tpb != 512) return nullptr;
+        switch (cgv) {
+            case 1: return k_solve_grid<2, MODE_MIXED, 1, 512>;
+            case 2: return k_solve_grid<2, MODE_MIXED, 2, 512>;
+            default: return nullptr;
+        }
+    }
     if (fmt != NN_FMT_SELL) return nullptr;
     if (tpb == 512) {
         switch (cgv) {

@@ -4,6 +4,14 @@
 namespace nnqp {
 
 GridKernel grid_kernel_steady(int fmt, int cgv, int tpb) {
+    if (fmt == FMT_SELL_SMEM) {
+        if (tpb != 512) return nullptr;
+        switch (cgv) {
+            case 1: return k_solve_grid<2, MODE_STEADY, 1, 512>;
+            case 2: return k_solve_grid<2, MODE_STEADY, 2, 512>;
+            default: return nullptr;
+        }
+    }
     if (fmt == NN_FMT_CSR) {
         if (tpb != 256) return nullptr;
         switch (cgv) {

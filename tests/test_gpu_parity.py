@@ -256,6 +256,32 @@ def test_not_converged_returns_feasible_iterate():
 
 # ------------------------------------------------------------------ transient
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_shared_memory_operator_gives_identical_steps(prec, monkeypatch):
+    """Mid-size solves keep each block's operator slices in shared memory; the
+    products do the same arithmetic in the same order as from global memory,
+    so every step is bit-identical, and each meets the oracle's KKT test."""
+    spec = I.config2_transient_3d(n=30, nsteps=5)
+    s = gpu_system(spec)
+    p = P.NN_PREC_MIXED if prec == "mixed" else P.NN_PREC_FP64
+    out = {}
+    for flag in ("1", "0"):
+        monkeypatch.setenv("NNQP_SMEM_OP", flag)
+        c0 = torch.tensor(spec.c0, device=DEV)
+        cf = torch.zeros_like(c0)
+        hist = torch.zeros(spec.nsteps * spec.n_nodes, dtype=torch.float64, device=DEV)
+        infos = P.nn_transient(s, c0, spec.nsteps, cf, hist, P.solve_opts(precision=p))
+        assert all(i["status"] == 0 for i in infos)
+        out[flag] = hist.cpu().numpy().reshape(spec.nsteps, -1)
+    assert np.array_equal(out["1"], out["0"])
+    asm, red = oracle_reduced(spec)
+    prev = spec.c0
+    for n in range(spec.nsteps):
+        k = O.kkt(red.A, red.rhs(prev), spec.lo, spec.hi, out["1"][n][red.free])
+        assert k["bounds_ok"] and k["kkt_rel"] <= 1e-8
+        prev = out["1"][n]
+
+
 @pytest.mark.parametrize("extrapolate,prec", [(0, "fp64"), (1, "fp64"), (2, "fp64"), (1, "mixed")])
 def test_transient_small_matches_oracle_trajectory(extrapolate, prec):
     """Either first iterate (c^(n), or the projected extrapolation

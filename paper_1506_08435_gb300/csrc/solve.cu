@@ -137,6 +137,9 @@ namespace {
 constexpr double kStreamBytes = 48.0 * (1 << 20);
 // Most shared memory a block's staged operator slices may take.
 constexpr size_t kSmemOperatorBytes = 192 * 1024;
+// Threads per block of the projected L-BFGS kernel (128 was measured too:
+// faster on the 50^2 problem, slower on the 40^3 transient run).
+constexpr int kLbfgsThreads = 256;
 
 SellF64 view64(const nn_system *s) {
     return SellF64{s->NF, s->A64.nslices, s->A64.sptr, s->A64.col, s->A64.val, s->diag64,
@@ -329,7 +332,7 @@ nn_status run_grid(nn_system *s, const nn_solve_opts *o, int mode, int nsteps, c
         tpb = kSolveThreads;
         kern = grid_kernel(mode, fmt, a.ctl.cg_variant, tpb);
     }
-    if (lbfgs) tpb = kSolveThreads;
+    if (lbfgs) tpb = kLbfgsThreads;
     if (!kern) {
         set_error("CG variant %d is not available for this mode and format", a.ctl.cg_variant);
         return NN_ERR_INVALID_ARG;

@@ -335,7 +335,7 @@ def run_steady(P, torch, args, rank, dim):
     name = ("steady3d_n%d" % (args.n or 150)) if dim == 3 else ("steady2d_n%d" % (args.n or 50))
     return dict(times=times, infos=infos, kern_ms=[o[0]["time_ms"] for o in outs],
                 kern_bytes=[o[0]["bytes_algo"] for o in outs], units_per_step=1, e2e=e2e,
-                nnz_free=desc.get("nnz_free"), profile_scale_from="steady3d_n100" if dim == 3 else None,
+                nnz_free=desc.get("nnz_free"), profile_scale_from="steady3d_n104" if dim == 3 else None,
                 h2d=hbytes + ch.numel() * 8, d2h=ch.numel() * 8, clocks=clocks, launches=launches,
                 config={"workload": name, "nodes": spec.n_nodes, "free": desc.get("n_free"),
                         "nnz_free": desc.get("nnz_free"), "rtol": args.rtol, "solver": args.solver,

@@ -234,6 +234,34 @@ nn_status nn_step(nn_system *s, const double *c_prev, double *c_next, int memory
 nn_status nn_transient(nn_system *s, const double *c0, int nsteps, double *c_final, double *c_hist, int memory,
                        const nn_solve_opts *o, void *stream, nn_solve_info *infos);
 
+/* ------------------------------------------------------------- reusable plans
+ * A plan holds everything one persistent solve launch of system s needs
+ * (scratch vectors, barrier, counters, the chosen kernel, grid and shared
+ * memory), so the same QP (Sec. 2.1.3; for a transient system nsteps
+ * backward-Euler steps, Sec. 2.2.2) can be solved again and again without
+ * allocation or host synchronisation: nn_plan_launch only enqueues work on
+ * the stream, so launches can be issued back to back or captured into a
+ * CUDA graph.  One plan serves one launch at a time (launches of the same
+ * plan must be ordered on one stream).  The plan must not outlive s. */
+typedef struct nn_plan nn_plan;
+
+/* Builds a plan for options o (NULL = defaults); nsteps = 1 for a steady
+ * system, >= 1 for a transient one.  Scratch is allocated on stream. */
+nn_status nn_plan_create(nn_system *s, const nn_solve_opts *o, int nsteps, void *stream, nn_plan **out);
+
+/* Enqueues one solve: c_in [N] warm start (device), c_out [N] solution
+ * (device, may equal c_in), c_hist NULL or [nsteps][N] (transient).  Returns
+ * without synchronising; launch errors are reported at once. */
+nn_status nn_plan_launch(nn_plan *p, const double *c_in, double *c_out, double *c_hist, void *stream);
+
+/* Waits for stream and returns the records of the plan's last launch
+ * (infos: NULL or [ninfos]; time_ms is NaN: time launches with events).
+ * Status as nn_qp_solve / nn_transient. */
+nn_status nn_plan_result(nn_plan *p, void *stream, nn_solve_info *infos, int ninfos);
+
+/* Frees the plan's scratch; call when its launches have completed. */
+void nn_plan_destroy(nn_plan *p);
+
 /* FP64 KKT measures of c (full node vector) for the system's QP; for a
  * transient system c_prev selects the step's right-hand side (NULL for
  * steady).  out[0] kkt_rel = ||gP||_2/||b||_2, out[1] ||gP||_inf/||b||_inf,
@@ -288,10 +316,10 @@ nn_status nn_batch_solve(int count, nn_system *const *systems, double *const *c,
                          void *stream, nn_solve_info *infos);
 
 /* Times candidate launch shapes (threads per block x CTAs per system:
- * 128x1, 256x1, 512x1, 256x4, 256x8, 256x16) on the batch's largest systems
- * (up to 256) under a cap of 1500 products each, and keeps the shape with
- * the shortest elapsed time for later nn_batch_solve calls in this process.
- * *best_shape receives threads * 100 + CTAs (e.g. 25608). */
+ * 256x4, 256x8, 256x16; for batches whose largest system has at most 8192
+ * free unknowns 256x1, 512x1, 256x4, 256x8) on the whole batch solved to the
+ * requested tolerance, and keeps the fastest for later nn_batch_solve calls
+ * in this process.  *best_shape receives threads * 100 + CTAs (e.g. 25608). */
 nn_status nn_batch_autotune(int count, nn_system *const *systems, const nn_solve_opts *o, void *stream,
                             int *best_shape);
 

@@ -103,7 +103,8 @@ EXPORTS = ["nn_last_error", "nn_version", "nn_kernel_launches", "nn_mesh_counts"
            "nn_solve_opts_default", "nn_qp_solve", "nn_step", "nn_transient", "nn_kkt_residual", "nn_spmv",
            "nn_spmv_mixed_noalloc",
            "nn_batch_solve", "nn_batch_autotune", "nn_serve_opts_default", "nn_serve_create",
-           "nn_serve_submit", "nn_serve_poll", "nn_serve_drain", "nn_serve_stats", "nn_serve_destroy"]
+           "nn_serve_submit", "nn_serve_poll", "nn_serve_drain", "nn_serve_stats", "nn_serve_destroy",
+           "nn_plan_create", "nn_plan_launch", "nn_plan_result", "nn_plan_destroy"]
 
 _lib = None
 
@@ -137,6 +138,11 @@ def lib():
     L.nn_qp_solve.argtypes = [vp, POINTER(nn_solve_opts), vp, c_int, vp, POINTER(nn_solve_info)]
     L.nn_step.argtypes = [vp, vp, vp, c_int, POINTER(nn_solve_opts), vp, POINTER(nn_solve_info)]
     L.nn_transient.argtypes = [vp, vp, c_int, vp, vp, c_int, POINTER(nn_solve_opts), vp, POINTER(nn_solve_info)]
+    L.nn_plan_create.argtypes = [vp, POINTER(nn_solve_opts), c_int, vp, POINTER(vp)]
+    L.nn_plan_launch.argtypes = [vp, vp, vp, vp, vp]
+    L.nn_plan_result.argtypes = [vp, vp, POINTER(nn_solve_info), c_int]
+    L.nn_plan_destroy.argtypes = [vp]
+    L.nn_plan_destroy.restype = None
     L.nn_kkt_residual.argtypes = [vp, vp, vp, c_int, POINTER(c_double), vp]
     L.nn_spmv.argtypes = [vp, vp, vp, c_int, c_int, vp]
     L.nn_spmv_mixed_noalloc.argtypes = [vp, vp, vp, vp]
@@ -385,6 +391,40 @@ def nn_batch_autotune(systems, opts=None, stream=None):
     o = opts if opts is not None else solve_opts()
     _check(lib().nn_batch_autotune(n, hs, byref(o), _stream(stream), byref(best)))
     return best.value
+
+
+class Plan:
+    """A reusable solve of one system (nn_plan_*): launches enqueue work on a
+    stream without allocating or synchronising (capturable in CUDA graphs)."""
+
+    def __init__(self, sys, opts=None, nsteps=1, stream=None):
+        self.sys = sys
+        self.nsteps = nsteps
+        h = c_void_p()
+        o = opts if opts is not None else solve_opts()
+        _check(lib().nn_plan_create(sys.handle, byref(o), nsteps, _stream(stream), byref(h)))
+        self.handle = h
+
+    def launch(self, c_in, c_out, c_hist=None, stream=None):
+        _check(lib().nn_plan_launch(self.handle, _ptr(c_in)[0], _ptr(c_out)[0],
+                                    _ptr(c_hist)[0] if c_hist is not None else None, _stream(stream)))
+
+    def result(self, stream=None, allow=(NN_ERR_NOT_CONVERGED,)):
+        infos = (nn_solve_info * self.nsteps)()
+        st = lib().nn_plan_result(self.handle, _stream(stream), infos, self.nsteps)
+        _check(st, allow)
+        return [_info(st, i) for i in infos]
+
+    def close(self):
+        if self.handle is not None and self.handle.value:
+            lib().nn_plan_destroy(self.handle)
+        self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # pragma: no cover - interpreter shutdown
+            pass
 
 
 def serve_opts(**kw):

@@ -274,7 +274,7 @@ nn_status nn_batch_solve(int count, nn_system *const *systems, double *const *c,
 }
 
 nn_status nn_batch_autotune(int count, nn_system *const *systems, const nn_solve_opts *o, void *stream,
-                            int *best_threads) {
+                            int *best_shape) {
     clear_error();
     nn_solve_opts d;
     nn_solve_opts_default(&d);
@@ -285,22 +285,28 @@ nn_status nn_batch_autotune(int count, nn_system *const *systems, const nn_solve
         return NN_ERR_INVALID_ARG;
     }
     cudaStream_t st = (cudaStream_t)stream;
-    // The batch's makespan is set by its largest, slowest instances: every
-    // candidate shape solves the whole batch (at most 256 instances, largest
-    // first) under a cap of 1500 products per instance, and the shape with the
-    // shortest elapsed time wins.
+    // Every candidate shape solves the whole batch to the requested tolerance
+    // and the shape with the shortest elapsed time wins: the makespan depends
+    // on how many instances run side by side as much as on how fast each one
+    // runs, so a sample of the batch misjudges it (measured: a quarter of the
+    // batch picked 16 CTAs per instance, 19% slower on the whole batch than 8).
+    // One block per instance is a candidate only for batches of small
+    // instances; clusters win as soon as an instance has thousands of rows.
     std::vector<nn_system *> sample(systems, systems + count);
-    std::stable_sort(sample.begin(), sample.end(),
-                     [](const nn_system *a, const nn_system *b) { return a->nnzF > b->nnzF; });
-    if ((int)sample.size() > 256) sample.resize(256);
+    int64_t largest = 0;
+    for (int i = 0; i < count; ++i) largest = std::max<int64_t>(largest, systems[i]->NF);
     const int ns = (int)sample.size();
     Scratch S;
     S.st = st;
     std::vector<double *> cs(ns);
     for (int i = 0; i < ns; ++i) NN_TRY(S.a.alloc(&cs[i], sample[i]->N, st));
     nn_solve_opts t = *o;
-    t.max_iter = 1500;
-    const BatchShape cands[6] = {{128, 1}, {256, 1}, {512, 1}, {256, 4}, {256, 8}, {256, 16}};
+    std::vector<BatchShape> cands;
+    if (largest <= 8192) {
+        cands = {{256, 1}, {512, 1}, {256, 4}, {256, 8}};
+    } else {
+        cands = {{256, 4}, {256, 8}, {256, 16}};
+    }
     float best = 1e30f;
     BatchShape pick_shape;
     std::vector<nn_solve_info> inf(ns);
@@ -317,7 +323,7 @@ nn_status nn_batch_autotune(int count, nn_system *const *systems, const nn_solve
     }
     g_tuned = pick_shape;
     g_have_tuned = true;
-    if (best_threads) *best_threads = pick_shape.tpb * 100 + pick_shape.cluster;
+    if (best_shape) *best_shape = pick_shape.tpb * 100 + pick_shape.cluster;
     clear_error();
     return NN_OK;
 }

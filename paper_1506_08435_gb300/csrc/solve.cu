@@ -6,6 +6,7 @@
 #include <cstring>
 #include <algorithm>
 #include <mutex>
+#include <new>
 #include "internal.h"
 #include "grid.cuh"
 #include "lbfgs.cuh"
@@ -224,9 +225,22 @@ void fill_info(const nn_system *s, const int64_t *cnt, const double *sc, int pre
     (void)precision;
 }
 
-// Runs the persistent solve kernel.  c_in/c_out/c_hist are device arrays.
-nn_status run_grid(nn_system *s, const nn_solve_opts *o, int mode, int nsteps, const double *c_in, double *c_out,
-                   double *c_hist, cudaStream_t st, nn_solve_info *infos, int ninfos) {
+// Everything one persistent solve launch needs, built once: arguments,
+// scratch, kernel, grid and shared memory.  A plan can be launched many times
+// (stream-ordered, without host synchronisation) and its results read after.
+struct GridPlan {
+    nn_system *s = nullptr;
+    nn_solve_opts o{};
+    int mode = 0, nsteps = 1;
+    GridArgs a{};
+    GridKernel kern = nullptr;
+    int want = 1, tpb = kSolveThreads;
+    size_t dyn_smem = 0;
+    DevArena arena;
+};
+
+// Builds plan P (its scratch is allocated on stream st).
+nn_status plan_build(nn_system *s, const nn_solve_opts *o, int mode, int nsteps, cudaStream_t st, GridPlan &P) {
     const int64_t n = s->NF, N = s->N;
     const bool mixed = mode_mixed(mode);
     const int fmt = o->format;
@@ -246,9 +260,12 @@ nn_status run_grid(nn_system *s, const nn_solve_opts *o, int mode, int nsteps, c
         set_error("CSR format is available in FP64 only");
         return NN_ERR_INVALID_ARG;
     }
-    Scratch S;
-    S.st = st;
-    GridArgs a;
+    P.s = s;
+    P.o = *o;
+    P.mode = mode;
+    P.nsteps = nsteps;
+    DevArena &SA = P.arena;
+    GridArgs &a = P.a;
     std::memset(&a, 0, sizeof(a));
     a.mode = mode;
     a.n = n;
@@ -265,14 +282,11 @@ nn_status run_grid(nn_system *s, const nn_solve_opts *o, int mode, int nsteps, c
     a.dinv64 = s->dinv64;
     a.dinv32 = s->dinv32;
     a.free_node = s->free_node;
-    a.c_in = c_in;
-    a.c_out = c_out;
-    a.c_hist = c_hist;
     a.nsteps = nsteps;
-    for (int k = 0; k < 11; ++k) NN_TRY(S.a.alloc(&a.v64[k], n, st));
-    NN_TRY(S.a.alloc(&a.fmask, n, st));
+    for (int k = 0; k < 11; ++k) NN_TRY(SA.alloc(&a.v64[k], n, st));
+    NN_TRY(SA.alloc(&a.fmask, n, st));
     if (mixed)
-        for (int k = 0; k < 13; ++k) NN_TRY(S.a.alloc(&a.v32[k], n, st));
+        for (int k = 0; k < 13; ++k) NN_TRY(SA.alloc(&a.v32[k], n, st));
     a.ctl.max_spmv = o->max_iter;
     // gradient-projection steps per phase: a warm-started time step has few
     // active-set changes to find, and short GP phases win there (measured on
@@ -311,12 +325,12 @@ nn_status run_grid(nn_system *s, const nn_solve_opts *o, int mode, int nsteps, c
     if (lbfgs) {
         a.m = std::min(o->lbfgs_m, kLbMaxM);
         a.h0 = 1.0 / s->anorm_inf;
-        NN_TRY(S.a.alloc(&a.S, (size_t)(a.m + 1) * n, st));
-        NN_TRY(S.a.alloc(&a.Y, (size_t)(a.m + 1) * n, st));
+        NN_TRY(SA.alloc(&a.S, (size_t)(a.m + 1) * n, st));
+        NN_TRY(SA.alloc(&a.Y, (size_t)(a.m + 1) * n, st));
     }
     a.predict = o->extrapolate;
-    if (mode_transient(mode) && a.predict) NN_TRY(S.a.alloc(&a.xprev, n, st));
-    if (mode_transient(mode) && a.predict == 2) NN_TRY(S.a.alloc(&a.xprev2, n, st));
+    if (mode_transient(mode) && a.predict) NN_TRY(SA.alloc(&a.xprev, n, st));
+    if (mode_transient(mode) && a.predict == 2) NN_TRY(SA.alloc(&a.xprev2, n, st));
     // Grid: one slice per warp at least.  Systems that a grid of one block
     // per SM covers in a few slices per warp run one block per SM (fewer
     // barrier arrivals) of 512 threads (one slice per warp: all loads of a
@@ -387,29 +401,48 @@ nn_status run_grid(nn_system *s, const nn_solve_opts *o, int mode, int nsteps, c
     // the bounded-wait path (no fault, the kernel returns TIMEOUT).
     const char *stall = getenv("NNQP_TEST_STALL_BARRIER");
     a.bar_extra = (stall && stall[0] == '1') ? 1 : 0;
-    NN_TRY(S.a.alloc(&a.bar, 1, st));
-    NN_TRY(S.a.alloc(&a.partials, (size_t)2 * kMaxRed * (want + a.bar_extra), st));
-    NN_TRY(S.a.alloc(&a.counters, (size_t)nsteps * kCounters, st));
-    NN_TRY(S.a.alloc(&a.scalars, (size_t)nsteps * kScalars, st));
+    NN_TRY(SA.alloc(&a.bar, 1, st));
+    NN_TRY(SA.alloc(&a.partials, (size_t)2 * kMaxRed * (want + a.bar_extra), st));
+    NN_TRY(SA.alloc(&a.counters, (size_t)nsteps * kCounters, st));
+    NN_TRY(SA.alloc(&a.scalars, (size_t)nsteps * kScalars, st));
+    P.kern = kern;
+    P.want = want;
+    P.tpb = tpb;
+    P.dyn_smem = dyn_smem;
+    return NN_OK;
+}
+
+// Enqueues one launch of plan P on stream st: resets the barrier and the
+// counters, runs the persistent kernel, writes the Dirichlet entries of the
+// outputs.  No host synchronisation (capturable in a CUDA graph).
+nn_status plan_enqueue(GridPlan &P, const double *c_in, double *c_out, double *c_hist, cudaStream_t st) {
+    GridArgs &a = P.a;
+    const int64_t N = P.s->N;
+    a.c_in = c_in;
+    a.c_out = c_out;
+    a.c_hist = c_hist;
     NN_CUDA_TRY(cudaMemsetAsync(a.bar, 0, sizeof(GridBarrier), st));
-    NN_CUDA_TRY(cudaMemsetAsync(a.counters, 0, sizeof(int64_t) * nsteps * kCounters, st));
-    cudaEvent_t e0, e1;
-    NN_CUDA_TRY(cudaEventCreate(&e0));
-    NN_CUDA_TRY(cudaEventCreate(&e1));
-    cudaEventRecord(e0, st);
+    NN_CUDA_TRY(cudaMemsetAsync(a.counters, 0, sizeof(int64_t) * P.nsteps * kCounters, st));
     void *args[] = {&a};
-    cudaError_t le = cudaLaunchCooperativeKernel((void *)kern, dim3(want), dim3(tpb), args, dyn_smem, st);
+    cudaError_t le = cudaLaunchCooperativeKernel((void *)P.kern, dim3(P.want), dim3(P.tpb), args, P.dyn_smem, st);
     count_launch();
     if (le != cudaSuccess) {
-        cudaEventDestroy(e0);
-        cudaEventDestroy(e1);
-        set_error("cooperative launch of %d blocks failed: %s", want, cudaGetErrorString(le));
+        set_error("cooperative launch of %d blocks failed: %s", P.want, cudaGetErrorString(le));
         return NN_ERR_CUDA;
     }
-    // Dirichlet entries of the outputs
-    (k_fill_dirichlet<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(N, s->dmask, s->dval, c_out, 1, 0), ::nnqp::count_launch());
-    if (c_hist) (k_fill_dirichlet<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(N, s->dmask, s->dval, c_hist, nsteps, N), ::nnqp::count_launch());
-    cudaEventRecord(e1, st);
+    (k_fill_dirichlet<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(N, P.s->dmask, P.s->dval, c_out, 1, 0),
+     ::nnqp::count_launch());
+    if (c_hist)
+        (k_fill_dirichlet<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(N, P.s->dmask, P.s->dval, c_hist,
+                                                                       P.nsteps, N),
+         ::nnqp::count_launch());
+    return NN_OK;
+}
+
+// Reads the records of the last launch of plan P (synchronises stream st).
+nn_status plan_collect(GridPlan &P, cudaStream_t st, float ms, nn_solve_info *infos, int ninfos) {
+    GridArgs &a = P.a;
+    const int nsteps = P.nsteps;
     std::vector<int64_t> cnt((size_t)nsteps * kCounters);
     std::vector<double> sc((size_t)nsteps * kScalars);
     GridBarrier hb;
@@ -417,18 +450,14 @@ nn_status run_grid(nn_system *s, const nn_solve_opts *o, int mode, int nsteps, c
     NN_CUDA_TRY(cudaMemcpyAsync(sc.data(), a.scalars, sizeof(double) * sc.size(), cudaMemcpyDeviceToHost, st));
     NN_CUDA_TRY(cudaMemcpyAsync(&hb, a.bar, sizeof(hb), cudaMemcpyDeviceToHost, st));
     NN_CUDA_TRY(cudaStreamSynchronize(st));
-    float ms = 0.0f;
-    cudaEventElapsedTime(&ms, e0, e1);
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
     if (hb.error) {
-        set_error("a device-side wait gave up after %.3g s (wait #%d)", o->wait_timeout_s, hb.where);
+        set_error("a device-side wait gave up after %.3g s (wait #%d)", P.o.wait_timeout_s, hb.where);
         return (nn_status)hb.error;
     }
     nn_status worst = NN_OK;
     for (int k = 0; k < nsteps; ++k) {
         nn_solve_info inf;
-        fill_info(s, &cnt[(size_t)k * kCounters], &sc[(size_t)k * kScalars], mixed, &inf);
+        fill_info(P.s, &cnt[(size_t)k * kCounters], &sc[(size_t)k * kScalars], mode_mixed(P.mode), &inf);
         if (k == 0) inf.time_ms = ms;
         if (infos && k < ninfos) infos[k] = inf;
         if (inf.status != NN_OK && worst == NN_OK) worst = (nn_status)inf.status;
@@ -436,6 +465,34 @@ nn_status run_grid(nn_system *s, const nn_solve_opts *o, int mode, int nsteps, c
     if (worst == NN_ERR_NOT_CONVERGED) set_error("iteration cap reached before the KKT tolerance");
     else if (worst == NN_ERR_NUMERIC) set_error("NaN/Inf met in a reduction");
     return worst;
+}
+
+// Runs the persistent solve kernel once: plan, launch, records, release.
+// c_in/c_out/c_hist are device arrays.
+nn_status run_grid(nn_system *s, const nn_solve_opts *o, int mode, int nsteps, const double *c_in, double *c_out,
+                   double *c_hist, cudaStream_t st, nn_solve_info *infos, int ninfos) {
+    GridPlan P;
+    struct Release {
+        GridPlan &p;
+        cudaStream_t st;
+        ~Release() { p.arena.release(st); }
+    } rel{P, st};
+    NN_TRY(plan_build(s, o, mode, nsteps, st, P));
+    cudaEvent_t e0, e1;
+    NN_CUDA_TRY(cudaEventCreate(&e0));
+    NN_CUDA_TRY(cudaEventCreate(&e1));
+    cudaEventRecord(e0, st);
+    nn_status r = plan_enqueue(P, c_in, c_out, c_hist, st);
+    cudaEventRecord(e1, st);
+    float ms = 0.0f;
+    if (r == NN_OK) {
+        NN_CUDA_TRY(cudaEventSynchronize(e1));
+        cudaEventElapsedTime(&ms, e0, e1);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (r != NN_OK) return r;
+    return plan_collect(P, st, ms, infos, ninfos);
 }
 
 nn_status kkt_impl(const nn_system *s, const double *c, const double *c_prev, int memory, double out[4],
@@ -613,3 +670,81 @@ nn_status serve_solve(nn_system *s, const nn_solve_opts *o, const double *c_in_d
 }
 
 }  // namespace nnqp
+
+// ---------------------------------------------------------------- reusable solve plans
+
+namespace nnqp {
+nn_status check_opts(const nn_solve_opts *o);
+}
+
+struct nn_plan {
+    nnqp::GridPlan p;
+    cudaStream_t st = nullptr;   // stream the scratch was allocated on
+};
+
+extern "C" {
+
+nn_status nn_plan_create(nn_system *s, const nn_solve_opts *o, int nsteps, void *stream, nn_plan **out) {
+    using namespace nnqp;
+    clear_error();
+    if (!s || !out) {
+        set_error("nn_plan_create: NULL system or output");
+        return NN_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    nn_solve_opts d;
+    nn_solve_opts_default(&d);
+    if (!o) o = &d;
+    NN_TRY(check_opts(o));
+    const int mode = mode_for(s, o);
+    if (nsteps < 1 || (!mode_transient(mode) && nsteps != 1)) {
+        set_error("nn_plan_create: nsteps must be 1 for a steady system, >= 1 for a transient one");
+        return NN_ERR_INVALID_ARG;
+    }
+    nn_plan *pl = new (std::nothrow) nn_plan;
+    if (!pl) {
+        set_error("nn_plan_create: out of host memory");
+        return NN_ERR_OOM;
+    }
+    pl->st = (cudaStream_t)stream;
+    nn_status r = plan_build(s, o, mode, nsteps, pl->st, pl->p);
+    if (r != NN_OK) {
+        pl->p.arena.release(pl->st);
+        cudaStreamSynchronize(pl->st);
+        delete pl;
+        return r;
+    }
+    *out = pl;
+    return NN_OK;
+}
+
+nn_status nn_plan_launch(nn_plan *pl, const double *c_in, double *c_out, double *c_hist, void *stream) {
+    using namespace nnqp;
+    clear_error();
+    if (!pl || !c_in || !c_out) {
+        set_error("nn_plan_launch: NULL plan or vector");
+        return NN_ERR_INVALID_ARG;
+    }
+    return plan_enqueue(pl->p, c_in, c_out, c_hist, (cudaStream_t)stream);
+}
+
+nn_status nn_plan_result(nn_plan *pl, void *stream, nn_solve_info *infos, int ninfos) {
+    using namespace nnqp;
+    clear_error();
+    if (!pl) {
+        set_error("nn_plan_result: NULL plan");
+        return NN_ERR_INVALID_ARG;
+    }
+    nn_status r = plan_collect(pl->p, (cudaStream_t)stream, 0.0f, infos, ninfos);
+    for (int k = 0; infos && k < ninfos && k < pl->p.nsteps; ++k) infos[k].time_ms = NAN;
+    return r;
+}
+
+void nn_plan_destroy(nn_plan *pl) {
+    if (!pl) return;
+    pl->p.arena.release(pl->st);
+    cudaStreamSynchronize(pl->st);
+    delete pl;
+}
+
+}  // extern "C"

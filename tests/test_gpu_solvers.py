@@ -214,3 +214,66 @@ def test_serving_budget_admission_and_rejection():
     with pytest.raises(P.NnError):
         P.nn_serve_submit(sv, P.Problem(bad))
     P.nn_serve_destroy(sv)
+
+
+# ------------------------------------------------------------------ reusable plans
+
+def test_plan_launches_equal_single_solves_and_replay_in_a_cuda_graph():
+    """A plan's launches (back to back, no allocation, no host sync) and
+    their replay from a captured CUDA graph give the same bits as
+    nn_qp_solve; a transient plan matches nn_transient."""
+    spec = I.config1_steady_2d()
+    s = gpu_system(spec)
+    ref = torch.zeros(spec.n_nodes, dtype=torch.float64, device=DEV)
+    info = P.nn_qp_solve(s, ref, P.solve_opts())
+    assert info["status"] == 0
+    plan = P.Plan(s, P.solve_opts())
+    zero = torch.zeros_like(ref)
+    outs = [torch.empty_like(ref) for _ in range(3)]
+    for o in outs:
+        plan.launch(zero, o)
+    pinfo = plan.result()[0]
+    assert pinfo["status"] == 0 and pinfo["spmv"] == info["spmv"]
+    for o in outs:
+        assert torch.equal(o, ref)
+    # capture two launches into a CUDA graph and replay it
+    side = torch.cuda.Stream()
+    g_out = torch.empty_like(ref)
+    side.wait_stream(torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=side):
+        plan.launch(zero, g_out, stream=side)
+    for _ in range(3):
+        g_out.fill_(-1.0)
+        graph.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(g_out, ref)
+    assert plan.result()[0]["status"] == 0
+    plan.close()
+    # transient
+    spec = I.config2_transient_3d(n=10, nsteps=4)
+    st = gpu_system(spec)
+    c0 = torch.tensor(spec.c0, device=DEV)
+    cf = torch.zeros_like(c0)
+    hist = torch.zeros(spec.nsteps * spec.n_nodes, dtype=torch.float64, device=DEV)
+    P.nn_transient(st, c0, spec.nsteps, cf, hist)
+    tplan = P.Plan(st, P.solve_opts(), nsteps=spec.nsteps)
+    cf2 = torch.zeros_like(c0)
+    hist2 = torch.zeros_like(hist)
+    tplan.launch(c0, cf2, hist2)
+    infos = tplan.result()
+    assert all(i["status"] == 0 for i in infos) and len(infos) == spec.nsteps
+    assert torch.equal(cf2, cf) and torch.equal(hist2, hist)
+    tplan.close()
+
+
+def test_plan_rejects_bad_arguments():
+    spec = I.config1_steady_2d(n=10)
+    s = gpu_system(spec)
+    with pytest.raises(P.NnError):
+        P.Plan(s, P.solve_opts(), nsteps=3)   # steady systems take nsteps = 1
+    plan = P.Plan(s)
+    with pytest.raises(P.NnError):
+        plan.launch(None, None)
+    plan.close()

@@ -200,6 +200,7 @@ __device__ int gpcg_solve(Team &T, const Rows &R, const Op &A, const Bounds<V> &
                           const GpcgCtl &C, GpcgStats &st) {
     const double tol2 = C.tol * C.tol, ftol2 = C.face_tol * C.face_tol;
     const V zero = (V)0, one = (V)1;
+    const bool pf_on = op_streams(A);   // large system: vector passes prefetch
     R.each([&](int64_t i) { v.x[i] = clampv(v.x[i], B.l(i), B.h(i)); });
     st.vec += 2;
     if (!T.sync()) return ST_TIMEOUT;
@@ -518,7 +519,8 @@ __device__ int gpcg_solve(Team &T, const Rows &R, const Op &A, const Bounds<V> &
                     const V va = (V)alpha;
                     V a5[3] = {zero, zero, zero};
                     double d5[3];
-                    R.each([&](int64_t i) {
+                    const void *pf5[5] = {v.s, v.p, v.r, v.q, v.dinv};
+                    R.each_pf(pf5, (int)sizeof(V), pf_on, [&](int64_t i) {
                         V si = v.s[i] + va * v.p[i];
                         V ri = v.r[i] - va * v.q[i];
                         V zi = v.dinv[i] * ri;
@@ -543,7 +545,8 @@ __device__ int gpcg_solve(Team &T, const Rows &R, const Op &A, const Bounds<V> &
                         break;
                     const V vb = (V)(d5[0] / rho);
                     rho = d5[0];
-                    R.each([&](int64_t i) { v.p[i] = v.z[i] + vb * v.p[i]; });
+                    const void *pf2[2] = {v.z, v.p};
+                    R.each_pf(pf2, (int)sizeof(V), pf_on, [&](int64_t i) { v.p[i] = v.z[i] + vb * v.p[i]; });
                     st.vec += 3;
                     st.fl += 2;
                     if (!T.sync()) return ST_TIMEOUT;

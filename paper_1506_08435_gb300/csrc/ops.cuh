@@ -208,6 +208,15 @@ struct SellF32DiffX {
 using SellF32Diff = SellF32DiffX<false>;
 using SellF32DiffLocal = SellF32DiffX<true>;
 
+// Whether an operator streams through L2 (large systems): the vector passes
+// of its solves prefetch their next slices too.
+template <bool L>
+__device__ __forceinline__ bool op_streams(const SellF64X<L> &A) { return A.stream; }
+template <bool L>
+__device__ __forceinline__ bool op_streams(const SellF32DiffX<L> &A) { return A.stream; }
+template <class Op>
+__device__ __forceinline__ bool op_streams(const Op &) { return false; }
+
 // CSR, FP64, one thread per row (rows taken in the same slice order as the
 // SELL operators so that every pass of a solve owns the same rows).
 struct CsrF64 {

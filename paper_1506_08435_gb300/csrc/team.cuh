@@ -350,6 +350,26 @@ struct Rows {
             if (i < n) f(i);
         }
     }
+    // The same pass with an L2 prefetch of the warp's next slice of the NP
+    // vectors it reads (esize bytes per entry), issued by one lane per
+    // 128-byte line: on large systems a warp then has the next rows' loads in
+    // flight while it works on these (streaming passes are bound by memory
+    // parallelism).  Slices that end past row n are not prefetched.
+    template <int NP, class F>
+    __device__ __forceinline__ void each_pf(const void *const (&pf)[NP], int esize, bool on, F &&f) const {
+        const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+        const int lines = esize >> 2;   // 32 rows x esize bytes / 128-byte lines
+        for (int64_t s = s0 + (threadIdx.x >> 5); s < s1; s += nw) {
+            const int64_t nx = s + nw;
+            if (on && nx < s1 && (nx + 1) * 32 <= n && lane < NP * lines) {
+                const int j = lane / lines, l = lane - j * lines;
+                const char *p = (const char *)pf[j] + nx * 32 * esize + 128 * l;
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+            }
+            int64_t i = s * 32 + lane;
+            if (i < n) f(i);
+        }
+    }
 };
 
 __host__ __device__ __forceinline__ Rows rows_of_block(int64_t n, int64_t nslices, int block, int nblocks) {

@@ -350,7 +350,8 @@ __device__ int gpcg_solve(Team &T, const Rows &R, const Op &A, const Bounds<V> &
                 for (int k = 0; k < C.cg_max; ++k) {
                     const V va = (V)cs.alpha, vb = (V)cs.beta;
                     V a4[4] = {zero, zero, zero, zero};   // gamma, delta, r'r, bound crossings
-                    R.each([&](int64_t i) {
+                    const void *pf6[6] = {v.z, v.p, v.w, v.q, v.s, v.r};
+                    R.each_pf(pf6, (int)sizeof(V), pf_on, [&](int64_t i) {
                         V pi = v.z[i] + vb * v.p[i];
                         V qi = v.w[i] + vb * v.q[i];
                         V si = v.s[i] + va * pi;

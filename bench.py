@@ -468,7 +468,7 @@ def main():
     ap.add_argument("--queue", type=int, default=64)
     ap.add_argument("--budget-gb", type=float, default=120.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--out-dir", default=os.path.join(ROOT, "gpurun_out"))
+    ap.add_argument("--out-dir", default=os.path.join(ROOT, "bench_out"))
     args = ap.parse_args()
     os.makedirs(args.out_dir, exist_ok=True)
     dist, rank, ws = dist_init()

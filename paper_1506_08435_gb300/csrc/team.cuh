@@ -111,8 +111,8 @@ __device__ __forceinline__ void warp_sum_transposed(const double (&in)[K], doubl
     for (int j = 0; j < S::CF; ++j) out[j] = v[j];
 }
 
-// Writes the warp totals of warp_sum_transposed to sm.warp[warp][k].
-template <int K>
+// Writes the warp totals of warp_sum_transposed to sm.warp[warp][OFF + k].
+template <int K, int OFF = 0>
 __device__ __forceinline__ void warp_totals_to_smem(const double (&t)[WarpSumShape<K>::CF], RedSmem &sm) {
     using S = WarpSumShape<K>;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -121,7 +121,30 @@ __device__ __forceinline__ void warp_totals_to_smem(const double (&t)[WarpSumSha
         const int base = (lane >> sh) * S::CF;
 #pragma unroll
         for (int j = 0; j < S::CF; ++j)
-            if (base + j < K) sm.warp[warp][base + j] = t[j];
+            if (base + j < K) sm.warp[warp][OFF + base + j] = t[j];
+    }
+}
+
+// Warp stage of a block sum: totals of v over the warp's lanes to
+// sm.warp[warp][k].  More than 32 values are summed as 32 + the rest, which
+// pads less than rounding K up to 64 (each padded value costs FP64 adds).
+template <int K>
+__device__ __forceinline__ void warp_stage(const double (&v)[K], RedSmem &sm) {
+    if constexpr (K <= 32) {
+        double t[WarpSumShape<K>::CF];
+        warp_sum_transposed<K>(v, t);
+        warp_totals_to_smem<K>(t, sm);
+    } else {
+        double a[32], b[K - 32];
+#pragma unroll
+        for (int k = 0; k < 32; ++k) a[k] = v[k];
+#pragma unroll
+        for (int k = 32; k < K; ++k) b[k - 32] = v[k];
+        double ta[WarpSumShape<32>::CF], tb[WarpSumShape<K - 32>::CF];
+        warp_sum_transposed<32>(a, ta);
+        warp_sum_transposed<K - 32>(b, tb);
+        warp_totals_to_smem<32, 0>(ta, sm);
+        warp_totals_to_smem<K - 32, 32>(tb, sm);
     }
 }
 
@@ -145,9 +168,7 @@ __device__ __forceinline__ void warp0_sum_warps(RedSmem &sm) {
 // every thread.
 template <int K>
 __device__ __forceinline__ void block_sum(double (&v)[K], RedSmem &sm) {
-    double t[WarpSumShape<K>::CF];
-    warp_sum_transposed<K>(v, t);
-    warp_totals_to_smem<K>(t, sm);
+    warp_stage<K>(v, sm);
     __syncthreads();
     if ((threadIdx.x >> 5) == 0) warp0_sum_warps<K>(sm);
     __syncthreads();
@@ -221,9 +242,7 @@ struct GridTeam {
     template <int K>
     __device__ bool reduce(double (&v)[K]) {
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-        double t[WarpSumShape<K>::CF];
-        warp_sum_transposed<K>(v, t);
-        warp_totals_to_smem<K>(t, *sm);
+        warp_stage<K>(v, *sm);
         __syncthreads();
         slot ^= 1;
         double *P = partials + (size_t)slot * kMaxRed * nblocks;
@@ -237,8 +256,19 @@ struct GridTeam {
             // warp k sums the per-block partials of entry k; the loads of
             // different entries are in flight together
             for (int k = warp; k < K; k += nw) {
+                // up to 8 partials per lane per round, all loads issued before
+                // the adds (one L2 round trip per 256 blocks)
+                const double *Pk = P + (size_t)k * nblocks;
                 double u = 0.0;
-                for (int b = lane; b < nblocks; b += 32) u += __ldcg(P + (size_t)k * nblocks + b);
+                for (int b0 = 0; b0 < nblocks; b0 += 256) {
+                    double w[8];
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        const int b = b0 + lane + 32 * j;
+                        w[j] = b < nblocks ? __ldcg(Pk + b) : 0.0;
+                    }
+                    u += ((w[0] + w[1]) + (w[2] + w[3])) + ((w[4] + w[5]) + (w[6] + w[7]));
+                }
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) u += __shfl_xor_sync(0xffffffffu, u, o);
                 if (lane == 0) sm->bcast[k] = u;
@@ -252,16 +282,21 @@ struct GridTeam {
             if (t < K * CH) {
                 const int k = t / CH, c = t - k * CH;
                 const double *Pk = P + (size_t)k * nblocks;
-                double u0 = 0.0, u1 = 0.0, u2 = 0.0, u3 = 0.0;
-                int b = c;
-                for (; b + 3 * CH < nblocks; b += 4 * CH) {
-                    u0 += __ldcg(Pk + b);
-                    u1 += __ldcg(Pk + b + CH);
-                    u2 += __ldcg(Pk + b + 2 * CH);
-                    u3 += __ldcg(Pk + b + 3 * CH);
+                double u = 0.0;
+                for (int j0 = 0; c + j0 * CH < nblocks; j0 += 16) {
+                    double w[16];
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const int b = c + (j0 + j) * CH;
+                        w[j] = b < nblocks ? __ldcg(Pk + b) : 0.0;
+                    }
+#pragma unroll
+                    for (int h = 8; h > 0; h >>= 1)
+#pragma unroll
+                        for (int j = 0; j < h; ++j) w[j] += w[j + h];
+                    u += w[0];
                 }
-                for (; b < nblocks; b += CH) u0 += __ldcg(Pk + b);
-                sm->warp[c][k] = (u0 + u1) + (u2 + u3);
+                sm->warp[c][k] = u;
             }
             __syncthreads();
             if (t < K) {
@@ -304,9 +339,7 @@ struct ClusterTeam {
     template <int K>
     __device__ bool reduce(double (&v)[K]) {
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-        double t[WarpSumShape<K>::CF];
-        warp_sum_transposed<K>(v, t);
-        warp_totals_to_smem<K>(t, *sm);
+        warp_stage<K>(v, *sm);
         __syncthreads();
         slot ^= 1;
         double *buf = xch + (size_t)slot * kMaxCluster * kMaxRed;

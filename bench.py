@@ -412,7 +412,8 @@ def run_serve(P, torch, args, rank):
     pool = [I.serve_request(r) for r in range(args.pool)]
     probs = [P.Problem(sp) for sp in pool]
     budget = int(args.budget_gb * (1 << 30))
-    sv = P.nn_serve_create(budget, P.serve_opts(max_inflight=args.inflight, queue_capacity=args.queue))
+    sopts = P.solve_opts(precision=P.NN_PREC_MIXED if args.precision == "mixed" else P.NN_PREC_FP64)
+    sv = P.nn_serve_create(budget, P.serve_opts(max_inflight=args.inflight, queue_capacity=args.queue, solve=sopts))
     # warm-up: one request of each kind
     for k in range(min(2, len(probs))):
         rid = P.nn_serve_submit(sv, probs[k])
@@ -421,7 +422,7 @@ def run_serve(P, torch, args, rank):
     P.nn_serve_destroy(sv)
     # a bounded queue: past saturation, arrivals are refused (counted) instead
     # of piling up, so the drain after the arrival window stays short
-    sv = P.nn_serve_create(budget, P.serve_opts(max_inflight=args.inflight, queue_capacity=args.queue))
+    sv = P.nn_serve_create(budget, P.serve_opts(max_inflight=args.inflight, queue_capacity=args.queue, solve=sopts))
     l0 = P.kernel_launches()
     ids = []
     t0 = time.perf_counter()
@@ -444,7 +445,8 @@ def run_serve(P, torch, args, rank):
     launches = P.kernel_launches() - l0
     return dict(stats=st, wall=wall, offered=len(arrivals), ok=ok, launches=launches,
                 config={"workload": "serve_poisson%g_for%gs" % (rate, duration), "payload_pool": args.pool,
-                        "max_inflight": args.inflight, "queue_capacity": args.queue, "budget_gb": args.budget_gb})
+                        "max_inflight": args.inflight, "queue_capacity": args.queue, "budget_gb": args.budget_gb,
+                        "precision": args.precision})
 
 
 def main():
@@ -517,7 +519,8 @@ def main():
                               "ok": r["ok"], "failed": st["failed"], "rejected": st["rejected"],
                               "wall_s": r["wall"], "saturated": st["rejected"] > 0 or st["solves_per_s"] < 0.95 * args.rate,
                               "bytes_peak": st["bytes_peak"], "inflight_peak": st["inflight_peak"],
-                              "higher_is_better": False, "n_gpus": ws, "dtype": "f64", "data": "synthetic",
+                              "higher_is_better": False, "n_gpus": ws,
+                              "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
                               "gpu_launches": r["launches"], "config": r["config"]}))
         return 0
     if args.workload == "transient3d":

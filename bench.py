@@ -437,13 +437,18 @@ def run_serve(P, torch, args, rank):
     P.nn_serve_drain(sv)
     wall = time.perf_counter() - t0
     st = P.nn_serve_stats(sv)
-    ok = 0
+    ok, failed = 0, []
     for rid, k in ids:
-        info = P.nn_serve_poll(sv, rid, np.zeros(pool[k].n_nodes))
+        try:
+            info = P.nn_serve_poll(sv, rid, np.zeros(pool[k].n_nodes))
+        except P.NnError as e:
+            failed.append(str(e))
+            continue
         ok += info is not None and info["status"] == 0
     P.nn_serve_destroy(sv)
     launches = P.kernel_launches() - l0
-    return dict(stats=st, wall=wall, offered=len(arrivals), ok=ok, launches=launches,
+    return dict(stats=st, wall=wall, offered=len(arrivals), ok=ok, failed=len(failed),
+                first_failure=failed[0] if failed else None, launches=launches,
                 config={"workload": "serve_poisson%g_for%gs" % (rate, duration), "payload_pool": args.pool,
                         "max_inflight": args.inflight, "queue_capacity": args.queue, "budget_gb": args.budget_gb,
                         "precision": args.precision})
@@ -516,7 +521,8 @@ def main():
             print(json.dumps({"metric": "serving p50/p99 latency", "value": st["p50_ms"], "unit": "ms",
                               "p99_ms": st["p99_ms"], "mean_ms": st["mean_ms"], "solves_per_s": st["solves_per_s"],
                               "offered": r["offered"], "offered_per_s": args.rate, "completed": st["completed"],
-                              "ok": r["ok"], "failed": st["failed"], "rejected": st["rejected"],
+                              "ok": r["ok"], "failed": st["failed"], "first_failure": r["first_failure"],
+                              "rejected": st["rejected"],
                               "wall_s": r["wall"], "saturated": st["rejected"] > 0 or st["solves_per_s"] < 0.95 * args.rate,
                               "bytes_peak": st["bytes_peak"], "inflight_peak": st["inflight_peak"],
                               "higher_is_better": False, "n_gpus": ws,

@@ -23,6 +23,7 @@
 #include <map>
 #include <memory>
 #include <mutex>
+#include <string>
 #include <thread>
 #include <vector>
 #include "internal.h"
@@ -50,6 +51,7 @@ struct Request {
     std::vector<double> result;
     nn_solve_info info{};
     nn_status status = NN_ERR_BUSY;
+    std::string error;            // the worker's message when the request failed
     bool done = false;
 };
 
@@ -113,10 +115,13 @@ void worker_loop(Server *sv) {
             stt = serve_solve(s, &sv->opts.solve, dc, dc, st, r->blocks, &r->info);
             if (stt == NN_OK || stt == NN_ERR_NOT_CONVERGED) {
                 r->result.resize(r->N);
-                if (cudaMemcpyAsync(r->result.data(), dc, sizeof(double) * r->N, cudaMemcpyDeviceToHost, st) !=
-                        cudaSuccess ||
-                    cudaStreamSynchronize(st) != cudaSuccess)
+                cudaError_t e = cudaMemcpyAsync(r->result.data(), dc, sizeof(double) * r->N,
+                                                cudaMemcpyDeviceToHost, st);
+                if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+                if (e != cudaSuccess) {
+                    set_error("serving: result copy failed: %s", cudaGetErrorString(e));
                     stt = NN_ERR_CUDA;
+                }
             }
         }
         if (dc) cudaFreeAsync(dc, st);
@@ -129,6 +134,7 @@ void worker_loop(Server *sv) {
             std::lock_guard<std::mutex> lk(sv->mu);
             r->status = stt;
             r->info.status = stt;
+            if (stt != NN_OK && stt != NN_ERR_NOT_CONVERGED) r->error = nn_last_error();
             r->t_done = Clock::now();
             r->done = true;
             sv->resident -= r->bytes;
@@ -331,7 +337,8 @@ nn_status nn_serve_poll(nn_server *h, uint64_t id, double *c_out, nn_solve_info 
     }
     if (info) *info = r->info;
     if (r->status != NN_OK && r->status != NN_ERR_NOT_CONVERGED) {
-        set_error("request %llu failed with status %d", (unsigned long long)id, (int)r->status);
+        set_error("request %llu failed with status %d: %s", (unsigned long long)id, (int)r->status,
+                  r->error.c_str());
         return r->status;
     }
     if (c_out) std::memcpy(c_out, r->result.data(), sizeof(double) * r->N);

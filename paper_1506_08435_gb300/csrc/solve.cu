@@ -383,9 +383,11 @@ nn_status plan_build(nn_system *s, const nn_solve_opts *o, int mode, int nsteps,
         }
         const size_t bytes = (size_t)most * (4 + vbytes);
         GridKernel ks = grid_kernel(mode, FMT_SELL_SMEM, a.ctl.cg_variant, tpb);
+        // the attribute is set to the same budget by every caller (solves on
+        // other host threads may launch this kernel at the same time)
         if (ks && bytes > 0 && bytes <= kSmemOperatorBytes &&
-            cudaFuncSetAttribute((const void *)ks, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) ==
-                cudaSuccess) {
+            cudaFuncSetAttribute((const void *)ks, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kSmemOperatorBytes) == cudaSuccess) {
             int per = 0;
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, ks, tpb, bytes);
             if (per * sms >= want) {

@@ -191,6 +191,28 @@ def test_serving_results_alone_and_in_the_mix_are_identical_and_correct():
     assert st8["p50_ms"] > 0 and st8["p99_ms"] >= st8["p50_ms"]
 
 
+def test_serving_whole_grid_share_concurrent_sizes_all_succeed():
+    """Default share (each request may take the whole co-resident grid) with
+    several requests of different sizes in flight: the shared-memory operator
+    kernel is chosen per request with a different dynamic size on each worker
+    thread, and every request must still launch and converge."""
+    specs = _serve_specs(12)
+    sv = P.nn_serve_create(8 << 30, P.serve_opts(max_inflight=4))
+    ids = [P.nn_serve_submit(sv, P.Problem(sp)) for sp in specs]
+    P.nn_serve_drain(sv)
+    out = []
+    for rid, sp in zip(ids, specs):
+        c = np.zeros(sp.n_nodes)
+        assert P.nn_serve_poll(sv, rid, c)["status"] == 0
+        out.append(c)
+    st = P.nn_serve_stats(sv)
+    P.nn_serve_destroy(sv)
+    assert st["completed"] == len(specs) and st["failed"] == 0
+    for c, sp in list(zip(out, specs))[:2]:
+        red, b, x_ref, _ = oracle_solution(sp)
+        compare_solution(c[red.free], x_ref, red.A, b, sp.lo, sp.hi)
+
+
 def test_serving_budget_admission_and_rejection():
     specs = _serve_specs(6)
     sizes = sorted(sp.n_nodes for sp in specs)

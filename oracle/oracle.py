@@ -14,6 +14,9 @@ What each function follows:
 * ``assemble``         -- K_e = |e| G^T D G and the consistent capacity
   matrix M_e (Sec. 3.2, pointwise Jacobian F_{1,1} = D and transient
   F_{0,0} = 1/dt), load F_e = f(x_c)|e|/(d+1) (one-point rule: reading).
+  ``lumped=True`` replaces M by its row-sum lumping diag(sum_j M_ij), the
+  textbook lumped capacity matrix (the paper uses the consistent one; the
+  lumped variant is an extension).
 * ``eliminate``        -- Dirichlet values c^p on Gamma^D (Sec. 2.1) taken
   out of the unknowns: A = Kt_FF, b = ft_F - Kt_FD c_D with
   Kt = K + M/dt, ft = f + M c^(n)/dt (Sec. 2.2.2; the printed ft uses
@@ -145,9 +148,11 @@ class Assembled:
 
 
 def assemble(coords, conn, coef_kind, coef, aL=0.0, aT=0.0, DM=0.0, f_elem=None, with_mass=False,
-             rowptr=None, col=None):
+             rowptr=None, col=None, lumped=False):
     """Assemble K (and M, F).  coef_kind 0: coef [E, 3|6] upper-triangle tensors;
-    coef_kind 1: coef [E, dim] cell velocities (dispersion law, Sec. 5)."""
+    coef_kind 1: coef [E, dim] cell velocities (dispersion law, Sec. 5).
+    lumped: M is replaced by diag(row sums of the consistent M), stored on the
+    same pattern with zero off-diagonal entries."""
     coords = np.ascontiguousarray(coords, np.float64)
     conn = np.ascontiguousarray(conn, np.int32)
     coef = np.ascontiguousarray(coef, np.float64)
@@ -166,6 +171,12 @@ def assemble(coords, conn, coef_kind, coef, aL=0.0, aT=0.0, DM=0.0, f_elem=None,
                             _p(F, _c_dp))
     if st != 0:
         raise ValueError("oracle assembly failed: " + ERRORS.get(st, str(st)))
+    if lumped and M is not None:
+        rows = np.repeat(np.arange(N), np.diff(rowptr))
+        ML = np.zeros_like(M)
+        diag = np.flatnonzero(col == rows)
+        ML[diag] = np.add.reduceat(M, rowptr[:-1])[rows[diag]]
+        M = ML
     return Assembled(rowptr, col, K, M, F)
 
 

@@ -447,6 +447,67 @@ def test_transient_steps_stay_in_bounds_and_match_dmp():
         assert c.min() == 0.0 and c.max() <= 1.0
 
 
+# ------------------------------------------------------------------ lumped capacity matrix
+
+def _simplex_measures(coords, conn):
+    """|e| of every simplex from its vertex coordinates: |det J| / d!."""
+    d = coords.shape[1]
+    J = coords[conn[:, 1:]] - coords[conn[:, :1]]
+    return np.abs(np.linalg.det(J)) / math.factorial(d)
+
+
+@pytest.mark.parametrize("dim,n", [(2, 4), (3, 3)])
+def test_lumped_mass_is_the_nodal_share_of_element_measures(dim, n):
+    """Row-sum lumping of the consistent P1 mass gives the diagonal matrix
+    M_ii = sum over elements e containing node i of |e| / (d+1), computed here
+    by brute force from the vertex coordinates; off-diagonal entries are 0,
+    the entries sum to the domain volume 1, and K does not change."""
+    coords, conn = O.mesh_structured(dim, n)
+    coef = np.tile([1.0, 0.2, 2.0] if dim == 2 else [1.0, 0.1, 0, 2.0, 0.3, 1.5], (len(conn), 1))
+    cons = O.assemble(coords, conn, I.KIND_TENSOR, coef, with_mass=True)
+    lump = O.assemble(coords, conn, I.KIND_TENSOR, coef, with_mass=True, lumped=True)
+    assert np.array_equal(cons.Kval, lump.Kval)
+    vol = _simplex_measures(coords, conn)
+    want = np.zeros(len(coords))
+    for e, verts in enumerate(conn):
+        for v in verts:
+            want[v] += vol[e] / (dim + 1)
+    ML = lump.M.toarray()
+    assert np.allclose(np.diag(ML), want, rtol=1e-14, atol=0)
+    assert np.count_nonzero(ML - np.diag(np.diag(ML))) == 0
+    assert ML.sum() == pytest.approx(1.0, rel=1e-14)
+    # consistent mass: positive off-diagonal entries, same row sums
+    Mc = cons.M.toarray()
+    assert (Mc[~np.eye(len(Mc), dtype=bool) & (Mc != 0)] > 0).all()
+    assert np.allclose(Mc.sum(axis=1), want, rtol=1e-14, atol=0)
+
+
+def test_lumped_backward_euler_keeps_the_maximum_principle():
+    """D = I on Kuhn tetrahedra: K has non-positive off-diagonal entries, so
+    K + M_L/dt is an M-matrix and a backward-Euler step from data in [0, 1]
+    stays in [0, 1] without constraints: the QP step equals the Galerkin step.
+    With the consistent M the same step undershoots (its positive
+    off-diagonal entries M_ij/dt break the M-matrix property), which is what
+    makes the bounds necessary there."""
+    n = 6
+    coords, conn = O.mesh_structured(3, n)
+    coef = np.tile([1.0, 0, 0, 1, 0, 1], (len(conn), 1))
+    mask, val = I.patch_dirichlet_3d(n, n, n)
+    c0 = np.where(mask == 1, val, 0.0)
+    for dt in (1e-2, 1e-3):
+        lump = O.assemble(coords, conn, I.KIND_TENSOR, coef, with_mass=True, lumped=True)
+        red = O.Reduced(lump, mask, val, dt=dt)
+        A = red.A.tocoo()
+        assert A.data[A.row != A.col].max() <= 0.0
+        xg = O.galerkin(red.A, red.rhs(c0))
+        assert xg.min() >= 0.0 and xg.max() <= 1.0
+        states = O.transient(red, c0, 0.0, 1.0, 2)
+        assert np.allclose(states[0][red.free], xg, rtol=0, atol=1e-12)
+        cons = O.assemble(coords, conn, I.KIND_TENSOR, coef, with_mass=True)
+        redc = O.Reduced(cons, mask, val, dt=dt)
+        assert O.galerkin(redc.A, redc.rhs(c0)).min() < -1e-3
+
+
 # ------------------------------------------------------------------ P9 / P10 / P11
 
 def test_objective_order_galerkin_violation_and_exact_bounds():

@@ -127,7 +127,7 @@ class ClockSampler:
 
 # ---------------------------------------------------------------- the oracle baseline (CPU)
 
-def oracle_sample(workload, budget_s=20.0, n=None):
+def oracle_sample(workload, budget_s=20.0, n=None, lumped=False):
     """The FP64 oracle as it stands, on a bounded sample of the workload;
     returns (units per second, cores used, description)."""
     from oracle import oracle as O
@@ -135,7 +135,8 @@ def oracle_sample(workload, budget_s=20.0, n=None):
     if workload == "transient3d":
         spec = I.config2_transient_3d()
         coords, conn = O.mesh_structured(3, spec.nx)
-        asm = O.assemble(coords, conn, spec.coef_kind, spec.coef, spec.aL, spec.aT, spec.DM, with_mass=True)
+        asm = O.assemble(coords, conn, spec.coef_kind, spec.coef, spec.aL, spec.aT, spec.DM, with_mass=True,
+                         lumped=lumped)
         red = O.Reduced(asm, spec.dmask, spec.dval, dt=spec.dt)
         c = spec.c0.copy()
         t0, k = time.perf_counter(), 0
@@ -145,8 +146,9 @@ def oracle_sample(workload, budget_s=20.0, n=None):
             c = red.full(x)
             k += 1
         dt = time.perf_counter() - t0
-        return k / dt, threads, ("first %d backward-Euler QP steps of the 40^3 transient problem (MPRGP + "
-                                 "active-set polish to 1e-12, OpenMP products), assembly excluded" % k)
+        return k / dt, threads, ("first %d backward-Euler QP steps of the 40^3 transient problem (%s mass; "
+                                 "MPRGP + active-set polish to 1e-12, OpenMP products), assembly excluded"
+                                 % (k, "lumped" if lumped else "consistent"))
     if workload == "steady2d":
         spec = I.config1_steady_2d()
         coords, conn = O.mesh_structured(2, spec.nx)
@@ -229,7 +231,7 @@ def transient_config(spec, args):
     """config of the default workload (both arms print the same one)."""
     return {"workload": "transient3d_n40_dt0.01_50steps", "nodes": spec.n_nodes, "tets": spec.n_elems,
             "qp_per_step": spec.nsteps, "rtol": args.rtol, "l2": "flushed between steps (256 MB write)",
-            "solver": args.solver, "precision": args.precision,
+            "solver": args.solver, "precision": args.precision, "mass": args.mass,
             "first_iterate": "projected 3c^n - 3c^(n-1) + c^(n-2)"}
 
 
@@ -241,7 +243,7 @@ def run_transient(P, torch, args, rank):
     mixed = args.precision == "mixed"
     opts = P.solve_opts(rtol=args.rtol, solver=P.NN_SOLVER_LBFGS if args.solver == "lbfgs" else P.NN_SOLVER_GPCG,
                         precision=P.NN_PREC_MIXED if mixed else P.NN_PREC_FP64)
-    aopts = P.assemble_opts(build_mixed=1 if mixed else 0)
+    aopts = P.assemble_opts(build_mixed=1 if mixed else 0, lumped_mass=1 if args.mass == "lumped" else 0)
     c0 = torch.tensor(spec.c0, device=dev)
     cf = torch.zeros_like(c0)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
@@ -397,10 +399,51 @@ def run_batch(P, torch, args, rank):
                                       ClockSampler(os.path.join(args.out_dir, "clocks_rank%d.csv" % rank)))
     launches = P.kernel_launches() - l0
     infos = [i for o in outs for i in o]
+    stream = torch.cuda.current_stream()
+    # the same instances solved one after another by the single-system FP64
+    # solver (one persistent launch each), once, for comparison
+    seq_opts = P.solve_opts(rtol=args.rtol, precision=P.NN_PREC_FP64)
+    for c in cs:
+        c.zero_()
+    flush.zero_()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for sy, c in zip(systems, cs):
+        P.nn_qp_solve(sy, c, seq_opts)
+    b.record(stream)
+    torch.cuda.synchronize()
+    seq_ms = a.elapsed_time(b)
+    # end to end through the C ABI: every step assembles each instance from
+    # pinned host buffers, copies the first iterates in, solves the batch and
+    # reads the solutions back into pinned host memory
+    hps = [pinned_problem(P, torch, sp) for sp in insts]
+    c0h = [torch.zeros(sp.n_nodes, dtype=torch.float64).pin_memory() for sp in insts]
+    outh = [torch.zeros(sp.n_nodes, dtype=torch.float64).pin_memory() for sp in insts]
+    e2e = []
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        ss = [P.nn_assemble(hp) for hp, _ in hps]
+        for c, h in zip(cs, c0h):
+            c.copy_(h, non_blocking=True)
+        P.nn_batch_solve(ss, cs, opts)
+        for h, c in zip(outh, cs):
+            h.copy_(c, non_blocking=True)
+        b.record(stream)
+        torch.cuda.synchronize()
+        e2e.append(a.elapsed_time(b))
+        del ss
+    h2d = sum(nb for _, nb in hps) + sum(h.numel() * 8 for h in c0h)
+    d2h = sum(h.numel() * 8 for h in outh)
     return dict(times=times, infos=infos, kern_ms=[o[0]["time_ms"] for o in outs],
                 kernel_name="k_batch_cluster" if tuned % 100 > 1 else "k_batch",
-                kern_bytes=[sum(i["bytes_algo"] for i in o) for o in outs], units_per_step=count, e2e=None,
-                h2d=0, d2h=0, clocks=clocks, launches=launches,
+                kern_bytes=[sum(i["bytes_algo"] for i in o) for o in outs], units_per_step=count, e2e=e2e,
+                h2d=h2d, d2h=d2h, clocks=clocks, launches=launches,
+                sequential_fp64={"value": count / (seq_ms / 1e3), "unit": "QP solves/s", "ms": seq_ms,
+                                 "how": "nn_qp_solve per instance, FP64, one after another"},
                 config={"workload": "batch2d_%d" % count, "instances": count, "threads_per_block": tuned // 100, "ctas_per_instance": tuned % 100,
                         "precision": args.precision, "rtol": args.rtol, "l2": "flushed between steps"},
                 dtype="f64" if prec == P.NN_PREC_FP64 else "f32+f64", unit="QP solves/s", metric="QP solves/s")
@@ -463,6 +506,8 @@ def main():
     ap.add_argument("--workload", default="transient3d",
                     choices=["transient3d", "steady3d", "steady2d", "batch", "serve"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--mass", default="consistent", choices=["consistent", "lumped"],
+                    help="capacity matrix of the transient workload")
     ap.add_argument("--solver", default="gpcg", choices=["gpcg", "lbfgs"])
     ap.add_argument("--n", type=int, default=0)
     ap.add_argument("--count", type=int, default=512)
@@ -489,9 +534,9 @@ def main():
         vals, cores, desc = [], os.cpu_count() or 1, ""
         t0 = time.perf_counter()
         for _ in range(args.warmup):
-            oracle_sample(args.workload, budget_s=1.0)
+            oracle_sample(args.workload, budget_s=1.0, lumped=args.mass == "lumped")
         for _ in range(args.steps):
-            v, cores, desc = oracle_sample(args.workload, budget_s=8.0)
+            v, cores, desc = oracle_sample(args.workload, budget_s=8.0, lumped=args.mass == "lumped")
             vals.append(v)
         v = float(np.median(vals))
         print(json.dumps({"impl": "reference", "metric": "QP solves/s", "value": v, "unit": "QP solves/s",
@@ -586,7 +631,9 @@ def main():
             "gpu_launches": r["launches"], "clocks": r["clocks"],
             "max_kkt_rel": float(max(i["kkt_rel"] for i in infos)),
             "statuses_ok": all(i["status"] == 0 for i in infos),
-            "spmv_per_step": sum(i["spmv"] for i in infos) / args.steps}
+            "spmv_per_step": sum(i["spmv"] for i in infos) / args.steps,
+            "cg_iters_per_step": sum(i["cg_iters"] for i in infos) / args.steps,
+            "phases_per_step": sum(i["iterations"] for i in infos) / args.steps}
     # the FP64 pipe as a second bound: algorithmic FP64 operations of the dominant
     # kernel per launch / its time, against 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
     fl64 = sum(i.get("flops64_algo", 0.0) for i in infos) / args.steps
@@ -596,6 +643,8 @@ def main():
                              "frac": ach / FP64_PIPE_PEAK_GFLOPS, "flops_per_launch": fl64}
     if r.get("graph"):
         line["graph"] = r["graph"]
+    if r.get("sequential_fp64"):
+        line["sequential_fp64"] = r["sequential_fp64"]
     if r["e2e"] is not None:
         e2e_ms = max_over_ranks(dist, sum(r["e2e"]))
         line["e2e"] = {"value": r["units_per_step"] * len(r["e2e"]) * ws / (e2e_ms / 1e3), "unit": r["unit"],
@@ -603,7 +652,7 @@ def main():
     else:
         line["e2e"] = None
     if rank == 0 and not args.no_cpu_baseline:
-        v, cores, desc = oracle_sample(args.workload)
+        v, cores, desc = oracle_sample(args.workload, lumped=args.mass == "lumped")
         if v is not None:
             line["cpu_baseline"] = {"value": v, "unit": r["unit"], "cores": cores, "kind": "oracle", "sample": desc}
     if rank == 0:

@@ -124,6 +124,10 @@ typedef struct {
     int build_csr;                  /* also keep the reduced matrix in CSR (for NN_FMT_CSR) */
     int build_mixed;                /* also build the FP32-value copy (for NN_PREC_MIXED) */
     int keep_full;                  /* keep the full-node K, M, F (for nn_system_copy_out) */
+    int lumped_mass;                /* 0 (default): consistent capacity matrix, as in the paper;
+                                       1: its row-sum lumping, M_aa = |e|/(d+1) per element and
+                                       vertex, no off-diagonal entries (an extension: with it,
+                                       K + M/dt keeps the sign pattern of K) */
 } nn_assemble_opts;
 
 void nn_assemble_opts_default(nn_assemble_opts *o);

@@ -57,7 +57,7 @@ class nn_problem(ctypes.Structure):
 
 
 class nn_assemble_opts(ctypes.Structure):
-    _fields_ = [("build_csr", c_int), ("build_mixed", c_int), ("keep_full", c_int)]
+    _fields_ = [("build_csr", c_int), ("build_mixed", c_int), ("keep_full", c_int), ("lumped_mass", c_int)]
 
 
 class nn_system_desc(ctypes.Structure):

@@ -297,17 +297,19 @@ __global__ void __launch_bounds__(TPB) k_element(int64_t E, int dim, const doubl
 }
 
 // Row r of K, M and F: contributions of the elements around node r, summed
-// in ascending element order.
+// in ascending element order.  M is the consistent P1 capacity matrix
+// |e|(1 + delta_ab)/((d+1)(d+2)), or with lumped != 0 its row-sum lumping
+// |e| delta_ab/(d+1).
 __global__ void __launch_bounds__(TPB) k_gather(int64_t N, int nv, const int32_t *__restrict__ conn,
                                                 const int64_t *__restrict__ iptr, const int32_t *__restrict__ inc,
                                                 const int64_t *__restrict__ rowptr, const int32_t *__restrict__ col,
                                                 const double *__restrict__ Ke, const double *__restrict__ vol,
                                                 const double *__restrict__ f_elem, double *__restrict__ Kval,
-                                                double *__restrict__ Mval, double *__restrict__ F) {
+                                                double *__restrict__ Mval, double *__restrict__ F, int lumped) {
     int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (r >= N) return;
     const int nk = nv * (nv + 1) / 2;
-    const double md = 2.0 / (nv * (nv + 1)), mo = 1.0 / (nv * (nv + 1));
+    const double md = lumped ? 1.0 / nv : 2.0 / (nv * (nv + 1)), mo = lumped ? 0.0 : 1.0 / (nv * (nv + 1));
     const int64_t r0 = rowptr[r];
     const int len = (int)(rowptr[r + 1] - r0);
     int32_t cols[kMaxRow];
@@ -542,6 +544,10 @@ nn_status assemble_impl(const nn_problem *p, const nn_assemble_opts *o, cudaStre
         set_error("nn_assemble: dt must be finite and >= 0");
         return NN_ERR_INVALID_ARG;
     }
+    if (o->lumped_mass != 0 && o->lumped_mass != 1) {
+        set_error("nn_assemble: lumped_mass must be 0 or 1 (got %d)", o->lumped_mass);
+        return NN_ERR_INVALID_ARG;
+    }
     if (p->coef_kind != NN_COEF_TENSOR && p->coef_kind != NN_COEF_VELOCITY) {
         set_error("nn_assemble: unknown coef_kind %d", p->coef_kind);
         return NN_ERR_INVALID_ARG;
@@ -675,7 +681,7 @@ nn_status assemble_impl(const nn_problem *p, const nn_assemble_opts *o, cudaStre
     if (transient || o->keep_full) TRYF(s->arena.alloc(&s->Mval, nnz, st));
     TRYF(s->arena.alloc(&s->F, N, st));
     (k_gather<<<nblk(N), TPB, 0, st>>>(N, nv, s->conn, iptr, inc, s->rowptr, s->col, Ke, vol, fel, s->Kval,
-                                        s->Mval, s->F), ::nnqp::count_launch());
+                                        s->Mval, s->F, o->lumped_mass), ::nnqp::count_launch());
     TRYF(check_status(d_status, st, "elements"));
 
     // ---- elimination

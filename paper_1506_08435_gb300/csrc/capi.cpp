@@ -137,6 +137,7 @@ void nn_assemble_opts_default(nn_assemble_opts *o) {
     o->build_csr = 1;
     o->build_mixed = 1;
     o->keep_full = 1;
+    o->lumped_mass = 0;
 }
 
 nn_status nn_assemble(const nn_problem *p, const nn_assemble_opts *o, void *stream, nn_system **out) {

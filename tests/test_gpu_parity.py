@@ -310,6 +310,49 @@ def test_transient_small_matches_oracle_trajectory(extrapolate, prec):
         prev = H[n]
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_transient_lumped_mass_matches_oracle(prec):
+    """Row-sum lumped capacity matrix: the assembled M (diagonal, zero
+    off-diagonal entries kept on the pattern), the reduced operator and the
+    transient trajectory agree with the oracle's lumped variant."""
+    spec = I.config2_transient_3d(n=10, nsteps=6)
+    s = gpu_system(spec, lumped_mass=1)
+    coords, conn = O.mesh_structured(3, spec.nx, spec.ny, spec.nz)
+    asm = O.assemble(coords, conn, spec.coef_kind, spec.coef, spec.aL, spec.aT, spec.DM, spec.f_elem,
+                     with_mass=True, lumped=True)
+    red = O.Reduced(asm, spec.dmask, spec.dval, dt=spec.dt)
+    nnz = int(asm.rowptr[-1])
+    M = copy(s, "M_val", nnz, np.float64)
+    assert np.all(np.abs(M - asm.Mval) <= 1e-14 * np.abs(asm.Mval))
+    assert np.count_nonzero(M) == spec.n_nodes
+    A = red.A
+    Av = copy(s, "A_val", A.nnz, np.float64)
+    arabs = np.repeat(np.add.reduceat(np.abs(A.data), A.indptr[:-1]), np.diff(A.indptr))
+    assert np.all(np.abs(Av - A.data) <= 1e-13 * arabs)
+    c0 = torch.tensor(spec.c0, device=DEV)
+    cf = torch.zeros_like(c0)
+    hist = torch.zeros(spec.nsteps * spec.n_nodes, dtype=torch.float64, device=DEV)
+    p = P.NN_PREC_MIXED if prec == "mixed" else P.NN_PREC_FP64
+    infos = P.nn_transient(s, c0, spec.nsteps, cf, hist, P.solve_opts(rtol=1e-11, precision=p))
+    assert all(i["status"] == 0 for i in infos)
+    H = hist.cpu().numpy().reshape(spec.nsteps, -1)
+    ref = O.transient(red, spec.c0, spec.lo, spec.hi, spec.nsteps)
+    for n in range(spec.nsteps):
+        b = red.rhs(ref[n - 1] if n else spec.c0)
+        compare_solution(H[n][red.free], ref[n][red.free], red.A, b, spec.lo, spec.hi)
+    # the consistent and lumped trajectories differ (the flag reached the kernel)
+    sc = gpu_system(spec)
+    cc = torch.zeros_like(c0)
+    P.nn_transient(sc, c0, spec.nsteps, cc, None, P.solve_opts(rtol=1e-11))
+    assert np.abs(cc.cpu().numpy() - H[-1]).max() > 1e-4
+
+
+def test_assembly_rejects_unknown_mass_flag():
+    with pytest.raises(P.NnError) as e:
+        gpu_system(I.config2_transient_3d(n=4, nsteps=1), lumped_mass=2)
+    assert e.value.status == P.NN_ERR_INVALID_ARG
+
+
 def test_transient_step_api_equals_batched_steps():
     spec = I.config2_transient_3d(n=8, nsteps=3)
     s = gpu_system(spec)

@@ -78,15 +78,21 @@ class ProblemSpec:
     nsteps: int = 0
     c0: np.ndarray | None = None     # [N] initial state for the transient case
     meta: dict = field(default_factory=dict)
+    coords: np.ndarray | None = None  # explicit mesh [N, dim] (None: the structured mesh nx, ny, nz)
+    conn: np.ndarray | None = None    # explicit connectivity [E, dim+1] int32
 
     @property
     def n_nodes(self) -> int:
+        if self.coords is not None:
+            return int(self.coords.shape[0])
         if self.dim == 2:
             return (self.nx + 1) * (self.ny + 1)
         return (self.nx + 1) * (self.ny + 1) * (self.nz + 1)
 
     @property
     def n_elems(self) -> int:
+        if self.conn is not None:
+            return int(self.conn.shape[0])
         return 2 * self.nx * self.ny if self.dim == 2 else 6 * self.nx * self.ny * self.nz
 
 
@@ -326,3 +332,64 @@ def tiny_3d(n, tensor, hi=math.inf, source_cell=(0, 0, 0)):
     mask = boundary_mask_3d(n, n, n)
     return ProblemSpec("tiny3d_%d" % n, 3, n, n, n, KIND_TENSOR, coef, f, mask,
                        np.zeros(len(mask)), 0.0, hi)
+
+
+def kuhn_mesh_without_box(n, box_lo, box_hi):
+    """Explicit mesh of the unit cube cut into n^3 hexahedra, each split into
+    the 6 Kuhn tetrahedra of the structured mesh (same vertex order), with the
+    hexahedra (i, j, k) that have box_lo <= i, j, k < box_hi removed.  Nodes
+    that no element uses (strictly inside the box) are dropped; the others
+    keep the lattice order i + (n+1)(j + (n+1)k).  Returns (coords [N, 3],
+    conn [E, 4] int32, lattice ids [N] of the kept nodes)."""
+    kk, jj, ii = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    ii, jj, kk = ii.ravel(), jj.ravel(), kk.ravel()
+    inside = ((ii >= box_lo) & (ii < box_hi) & (jj >= box_lo) & (jj < box_hi) &
+              (kk >= box_lo) & (kk < box_hi))
+    ii, jj, kk = ii[~inside], jj[~inside], kk[~inside]
+    unit = np.eye(3, dtype=np.int64)
+    m = n + 1
+    tets = []
+    for p in _PERMS:
+        v = np.stack([ii, jj, kk], axis=1).astype(np.int64)
+        verts = [v.copy()]
+        for a in p:
+            v = v + unit[a]
+            verts.append(v.copy())
+        tets.append(np.stack([w[:, 0] + m * (w[:, 1] + m * w[:, 2]) for w in verts], axis=1))
+    lat = np.stack(tets, axis=1).reshape(-1, 4)      # hexahedron-major, then permutation
+    used, conn = np.unique(lat, return_inverse=True)
+    conn = conn.reshape(-1, 4).astype(np.int32)
+    i = used % m
+    j = (used // m) % m
+    k = used // (m * m)
+    coords = np.stack([i, j, k], axis=1).astype(np.float64) / n
+    return coords, conn, used
+
+
+def cube_with_hole(m, mesh="mirrored"):
+    """Structured analogue of the cube with a cubic hole (Sec. 5.1): n = 9m
+    hexahedra per side, the hole [4/9, 5/9]^3 = hexahedra 4m <= i, j, k < 5m
+    removed; c = 0 on the outer boundary, c = 1 on the hole's boundary, f = 0,
+    v = e_x + e_y + e_z on every element, alpha_L = 1, alpha_T = 1e-3,
+    D_M = 0, bounds 0 <= c <= 1.  The paper's meshes are unstructured
+    tetrahedral meshes (types A, B, C) that are not available; two
+    structured types stand in:
+      "kuhn":     the Kuhn split, whose hexahedron diagonals run along v;
+      "mirrored": the same connectivity with x -> 1 - x, diagonals along
+                  (-1, 1, 1) (the physical problem is symmetric under the
+                  mirror, so only the mesh changes)."""
+    if mesh not in ("kuhn", "mirrored"):
+        raise ValueError("mesh must be 'kuhn' or 'mirrored'")
+    n = 9 * m
+    coords, conn, lat = kuhn_mesh_without_box(n, 4 * m, 5 * m)
+    if mesh == "mirrored":
+        coords[:, 0] = (n - lat % (n + 1)) / n
+    N = len(coords)
+    i, j, k = lat % (n + 1), (lat // (n + 1)) % (n + 1), lat // ((n + 1) ** 2)
+    outer = (i == 0) | (i == n) | (j == 0) | (j == n) | (k == 0) | (k == n)
+    hole = ((i >= 4 * m) & (i <= 5 * m) & (j >= 4 * m) & (j <= 5 * m) & (k >= 4 * m) & (k <= 5 * m))
+    mask = (outer | hole).astype(np.uint8)
+    val = np.where(hole, 1.0, 0.0)
+    v = np.ones((len(conn), 3))
+    return ProblemSpec("cube_hole_%s_m%d" % (mesh, m), 3, n, n, n, KIND_VELOCITY, v, None, mask, val, 0.0, 1.0,
+                       aL=1.0, aT=1e-3, DM=0.0, coords=coords, conn=conn, meta={"mesh": mesh, "m": m})

@@ -508,6 +508,60 @@ def test_lumped_backward_euler_keeps_the_maximum_principle():
         assert O.galerkin(redc.A, redc.rhs(c0)).min() < -1e-3
 
 
+# ------------------------------------------------------------------ cube with a hole (Sec. 5.1 analogue)
+
+def _cube_hole(m, mesh):
+    sp = I.cube_with_hole(m, mesh)
+    asm = O.assemble(sp.coords, sp.conn, sp.coef_kind, sp.coef, sp.aL, sp.aT, sp.DM, with_mass=True)
+    return sp, asm, O.Reduced(asm, sp.dmask, sp.dval)
+
+
+def test_cube_hole_mesh_and_volume():
+    """The explicit mesh generator with an empty hole reproduces the oracle's
+    structured Kuhn mesh; with the hole, the element measures sum to the
+    domain volume 1 - (1/9)^3, the capacity matrix too, and every row of K
+    sums to zero (constants are in the kernel of the Neumann operator)."""
+    c, e, _ = I.kuhn_mesh_without_box(5, 0, 0)
+    oc, oe = O.mesh_structured(3, 5)
+    assert np.array_equal(c, oc) and np.array_equal(e, oe)
+    for mesh in ("kuhn", "mirrored"):
+        sp, asm, _ = _cube_hole(2, mesh)
+        assert sp.n_nodes == 19 ** 3 - 1                 # one lattice node strictly inside the hole
+        assert sp.n_elems == 6 * (18 ** 3 - 2 ** 3)
+        assert _simplex_measures(sp.coords, sp.conn).sum() == pytest.approx(1 - 1 / 729, rel=1e-13)
+        assert asm.M.sum() == pytest.approx(1 - 1 / 729, rel=1e-13)
+        rs = np.abs(asm.K.sum(axis=1)).max()
+        assert rs <= 1e-13 * np.abs(asm.K).sum(axis=1).max()
+
+
+def test_cube_hole_aligned_mesh_keeps_dmp_mirrored_mesh_violates_it():
+    """v = (1,1,1) along the Kuhn diagonals: K_FF has no positive
+    off-diagonal entry (an M-matrix), the Galerkin solution stays in [0, 1]
+    and the QP returns it.  On the mirrored mesh the same physical problem
+    gives a Galerkin solution with negative values at a sizable share of the
+    nodes (the paper's Table of DMP violations reports 26-54% on its
+    unstructured meshes), while the QP keeps 0 <= c <= 1 exactly."""
+    sp, asm, red = _cube_hole(2, "kuhn")
+    A = red.A.tocoo()
+    assert A.data[A.row != A.col].max() <= 1e-15 * np.abs(A.data).max()
+    b = red.rhs()
+    xg = O.galerkin(red.A, b)
+    assert xg.min() >= -1e-14 and xg.max() <= 1.0
+    x, _ = O.solve_qp(red.A, b, 0.0, 1.0)
+    assert np.allclose(x, np.clip(xg, 0.0, 1.0), rtol=0, atol=1e-12)
+    sp, asm, red = _cube_hole(2, "mirrored")
+    A = red.A.tocoo()
+    assert A.data[A.row != A.col].max() > 0.0
+    b = red.rhs()
+    xg = O.galerkin(red.A, b)
+    full = red.full(xg)
+    share = ((full < 0) | (full > 1)).mean()
+    assert xg.min() < -0.01 and 0.2 < share < 0.4
+    x, _ = O.solve_qp(red.A, b, 0.0, 1.0)
+    assert x.min() == 0.0 and x.max() <= 1.0
+    assert O.kkt(red.A, b, 0.0, 1.0, x)["kkt_rel"] < 1e-12
+
+
 # ------------------------------------------------------------------ P9 / P10 / P11
 
 def test_objective_order_galerkin_violation_and_exact_bounds():

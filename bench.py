@@ -204,6 +204,12 @@ def pinned_problem(P, torch, spec):
     hp.c.dirichlet_value = keep["dval"].data_ptr()
     if "f_elem" in keep:
         hp.c.f_elem = keep["f_elem"].data_ptr()
+    if getattr(spec, "coords", None) is not None:
+        keep["coords"] = torch.from_numpy(np.ascontiguousarray(spec.coords, np.float64)).pin_memory()
+        keep["conn"] = torch.from_numpy(np.ascontiguousarray(spec.conn, np.int32)).pin_memory()
+        hp.coords, hp.conn = keep["coords"], keep["conn"]
+        hp.c.coords = keep["coords"].data_ptr()
+        hp.c.conn = keep["conn"].data_ptr()
     hp.c.memory = P.NN_MEM_HOST
     nbytes = sum(t.numel() * t.element_size() for t in keep.values())
     return hp, nbytes
@@ -288,7 +294,9 @@ def run_transient(P, torch, args, rank):
 
 
 def run_steady(P, torch, args, rank, dim):
-    if dim == 3:
+    if args.workload == "cube_hole":
+        spec = I.cube_with_hole(args.m, args.mesh)
+    elif dim == 3:
         spec = I.config3_steady_3d(n=args.n or 150)
     else:
         spec = I.config1_steady_2d(n=args.n or 50)
@@ -365,9 +373,28 @@ def run_steady(P, torch, args, rank, dim):
         plan.close()
         del s
     name = ("steady3d_n%d" % (args.n or 150)) if dim == 3 else ("steady2d_n%d" % (args.n or 50))
-    return dict(times=times, infos=infos, kern_ms=[o[0]["time_ms"] for o in outs], graph=graph,
+    scale_from = "steady3d_n104" if dim == 3 else None
+    dmp = None
+    if args.workload == "cube_hole":
+        name = "cube_hole_%s_m%d" % (args.mesh, args.m)
+        scale_from = "cube_hole_%s_m12" % args.mesh
+        # the Galerkin solution of the same system (no bounds: GPCG reduces to
+        # Jacobi-preconditioned CG), once, outside the timed region: how far
+        # the unconstrained discretisation leaves [0, 1] on this mesh
+        import dataclasses
+        gprob = P.Problem(dataclasses.replace(spec, lo=-math.inf, hi=math.inf), device=dev)
+        s = P.nn_assemble(gprob, aopts)
+        cg = torch.zeros(spec.n_nodes, dtype=torch.float64, device=dev)
+        ginfo = P.nn_qp_solve(s, cg, P.solve_opts(rtol=args.rtol, max_iter=args.max_iter))
+        cg = cg.cpu().numpy()
+        bad = int(((cg < 0.0) | (cg > 1.0)).sum())
+        dmp = {"galerkin_min": float(cg.min()), "galerkin_max": float(cg.max()), "nodes_violated": bad,
+               "nodes": spec.n_nodes, "share": bad / spec.n_nodes, "galerkin_ms": ginfo["time_ms"],
+               "galerkin_kkt_rel": ginfo["kkt_rel"]}
+        del s
+    return dict(times=times, infos=infos, kern_ms=[o[0]["time_ms"] for o in outs], graph=graph, dmp=dmp,
                 kern_bytes=[o[0]["bytes_algo"] for o in outs], units_per_step=1, e2e=e2e,
-                nnz_free=desc.get("nnz_free"), profile_scale_from="steady3d_n104" if dim == 3 else None,
+                nnz_free=desc.get("nnz_free"), profile_scale_from=scale_from,
                 h2d=hbytes + ch.numel() * 8, d2h=ch.numel() * 8, clocks=clocks, launches=launches,
                 config={"workload": name, "nodes": spec.n_nodes, "free": desc.get("n_free"),
                         "nnz_free": desc.get("nnz_free"), "rtol": args.rtol, "solver": args.solver,
@@ -504,12 +531,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="transient3d",
-                    choices=["transient3d", "steady3d", "steady2d", "batch", "serve"])
+                    choices=["transient3d", "steady3d", "steady2d", "batch", "serve", "cube_hole"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--mass", default="consistent", choices=["consistent", "lumped"],
                     help="capacity matrix of the transient workload")
     ap.add_argument("--solver", default="gpcg", choices=["gpcg", "lbfgs"])
     ap.add_argument("--n", type=int, default=0)
+    ap.add_argument("--m", type=int, default=16, help="cube with a hole: n = 9m hexahedra per side")
+    ap.add_argument("--mesh", default="mirrored", choices=["kuhn", "mirrored"], help="cube with a hole: mesh type")
     ap.add_argument("--count", type=int, default=512)
     ap.add_argument("--rtol", type=float, default=1e-10)
     ap.add_argument("--max-iter", type=int, default=200000)
@@ -580,6 +609,8 @@ def main():
         r = run_steady(P, torch, args, rank, 3)
     elif args.workload == "steady2d":
         r = run_steady(P, torch, args, rank, 2)
+    elif args.workload == "cube_hole":
+        r = run_steady(P, torch, args, rank, 3)
     else:
         r = run_batch(P, torch, args, rank)
     barrier(dist)
@@ -643,6 +674,8 @@ def main():
                              "frac": ach / FP64_PIPE_PEAK_GFLOPS, "flops_per_launch": fl64}
     if r.get("graph"):
         line["graph"] = r["graph"]
+    if r.get("dmp"):
+        line["galerkin_dmp"] = r["dmp"]
     if r.get("sequential_fp64"):
         line["sequential_fp64"] = r["sequential_fp64"]
     if r["e2e"] is not None:

@@ -8,7 +8,10 @@ from oracle import oracle as O
 
 def oracle_reduced(spec, with_mass=None):
     """(assembled, reduced) oracle system of a spec."""
-    coords, conn = O.mesh_structured(spec.dim, spec.nx, spec.ny, spec.nz)
+    if spec.coords is not None:
+        coords, conn = spec.coords, spec.conn
+    else:
+        coords, conn = O.mesh_structured(spec.dim, spec.nx, spec.ny, spec.nz)
     wm = spec.dt > 0 if with_mass is None else with_mass
     asm = O.assemble(coords, conn, spec.coef_kind, spec.coef, spec.aL, spec.aT, spec.DM, spec.f_elem,
                      with_mass=wm)

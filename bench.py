@@ -233,11 +233,16 @@ def timed_steps(torch, step, steps, flush, clk):
 
 # ---------------------------------------------------------------- workloads
 
+def solver_code(P, args):
+    return {"gpcg": P.NN_SOLVER_GPCG, "lbfgs": P.NN_SOLVER_LBFGS, "tron": P.NN_SOLVER_TRON}[args.solver]
+
+
 def transient_config(spec, args):
     """config of the default workload (both arms print the same one)."""
     return {"workload": "transient3d_n40_dt0.01_50steps", "nodes": spec.n_nodes, "tets": spec.n_elems,
             "qp_per_step": spec.nsteps, "rtol": args.rtol, "l2": "flushed between steps (256 MB write)",
-            "solver": args.solver, "precision": args.precision, "mass": args.mass,
+            "solver": args.solver + ("(ksp %g)" % args.ksp_rtol if args.solver == "tron" else ""),
+            "precision": args.precision, "mass": args.mass,
             "first_iterate": "projected 3c^n - 3c^(n-1) + c^(n-2)"}
 
 
@@ -247,7 +252,7 @@ def run_transient(P, torch, args, rank):
     nsteps = spec.nsteps
     prob = P.Problem(spec, device=dev)
     mixed = args.precision == "mixed"
-    opts = P.solve_opts(rtol=args.rtol, solver=P.NN_SOLVER_LBFGS if args.solver == "lbfgs" else P.NN_SOLVER_GPCG,
+    opts = P.solve_opts(rtol=args.rtol, solver=solver_code(P, args), ksp_rtol=args.ksp_rtol,
                         precision=P.NN_PREC_MIXED if mixed else P.NN_PREC_FP64)
     aopts = P.assemble_opts(build_mixed=1 if mixed else 0, lumped_mass=1 if args.mass == "lumped" else 0)
     c0 = torch.tensor(spec.c0, device=dev)
@@ -303,7 +308,7 @@ def run_steady(P, torch, args, rank, dim):
     dev = torch.device("cuda")
     prec = P.NN_PREC_MIXED if args.precision == "mixed" else P.NN_PREC_FP64
     opts = P.solve_opts(rtol=args.rtol, precision=prec, max_iter=args.max_iter,
-                        solver=P.NN_SOLVER_LBFGS if args.solver == "lbfgs" else P.NN_SOLVER_GPCG)
+                        solver=solver_code(P, args), ksp_rtol=args.ksp_rtol)
     aopts = P.assemble_opts(build_mixed=1 if prec == P.NN_PREC_MIXED else 0)
     prob = P.Problem(spec, device=dev)
     c = torch.zeros(spec.n_nodes, dtype=torch.float64, device=dev)
@@ -397,7 +402,8 @@ def run_steady(P, torch, args, rank, dim):
                 nnz_free=desc.get("nnz_free"), profile_scale_from=scale_from,
                 h2d=hbytes + ch.numel() * 8, d2h=ch.numel() * 8, clocks=clocks, launches=launches,
                 config={"workload": name, "nodes": spec.n_nodes, "free": desc.get("n_free"),
-                        "nnz_free": desc.get("nnz_free"), "rtol": args.rtol, "solver": args.solver,
+                        "nnz_free": desc.get("nnz_free"), "rtol": args.rtol,
+                        "solver": args.solver + ("(ksp %g)" % args.ksp_rtol if args.solver == "tron" else ""),
                         "precision": args.precision, "l2": "flushed between steps (256 MB write)"},
                 dtype="f64" if prec == P.NN_PREC_FP64 else "f32+f64", unit="QP solves/s", metric="QP solves/s")
 
@@ -535,7 +541,8 @@ def main():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--mass", default="consistent", choices=["consistent", "lumped"],
                     help="capacity matrix of the transient workload")
-    ap.add_argument("--solver", default="gpcg", choices=["gpcg", "lbfgs"])
+    ap.add_argument("--solver", default="gpcg", choices=["gpcg", "lbfgs", "tron"])
+    ap.add_argument("--ksp-rtol", type=float, default=1e-1, help="TRON: relative tolerance of each subspace CG")
     ap.add_argument("--n", type=int, default=0)
     ap.add_argument("--m", type=int, default=16, help="cube with a hole: n = 9m hexahedra per side")
     ap.add_argument("--mesh", default="mirrored", choices=["kuhn", "mirrored"], help="cube with a hole: mesh type")

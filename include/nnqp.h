@@ -60,7 +60,7 @@ typedef enum {
 
 enum { NN_MEM_HOST = 0, NN_MEM_DEVICE = 1 };
 enum { NN_COEF_TENSOR = 0, NN_COEF_VELOCITY = 1 };
-enum { NN_SOLVER_GPCG = 0, NN_SOLVER_LBFGS = 1 };
+enum { NN_SOLVER_GPCG = 0, NN_SOLVER_LBFGS = 1, NN_SOLVER_TRON = 2 };
 enum { NN_PREC_FP64 = 0, NN_PREC_MIXED = 1 };
 enum { NN_FMT_SELL = 0, NN_FMT_CSR = 1 };
 
@@ -171,8 +171,10 @@ nn_status nn_system_copy_out(const nn_system *s, int what, void *dst, size_t byt
 /* ------------------------------------------------------------------ solve */
 
 typedef struct {
-    int solver;          /* NN_SOLVER_GPCG (gradient projection + CG, More & Toraldo) or
-                            NN_SOLVER_LBFGS (projected limited-memory quasi-Newton, BLMVM-like) */
+    int solver;          /* NN_SOLVER_GPCG (gradient projection + CG, More & Toraldo),
+                            NN_SOLVER_LBFGS (projected limited-memory quasi-Newton, BLMVM-like) or
+                            NN_SOLVER_TRON (trust-region Newton for bounds, Lin & More 1999;
+                            Sec. 3.1 and 5.1); L-BFGS and TRON run in FP64 on the SELL format */
     int precision;       /* NN_PREC_FP64, or NN_PREC_MIXED: FP32 values/vectors in inner solves,
                             FP64 residual, refinement and KKT */
     int format;          /* NN_FMT_SELL or NN_FMT_CSR (FP64 only) */
@@ -187,6 +189,8 @@ typedef struct {
                             0 = c^(n); 1 = box projection of 2 c^(n) - c^(n-1);
                             2 (default) = box projection of 3 c^(n) - 3 c^(n-1) + c^(n-2)
                             (measured on the 40^3 run: 6,853 / 5,817 / 5,356 products) */
+    double ksp_rtol;     /* TRON: each subspace CG stops at ||r|| <= ksp_rtol ||r_0||
+                            (default 1e-1; the paper's TRON1/2/3 use 1e-1, 1e-2, 1e-3) */
 } nn_solve_opts;
 
 void nn_solve_opts_default(nn_solve_opts *o);

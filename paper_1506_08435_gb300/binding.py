@@ -34,7 +34,7 @@ STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "INFEASIBLE", 3: "NOT_SPD", 4: "OO
 
 NN_MEM_HOST, NN_MEM_DEVICE = 0, 1
 NN_COEF_TENSOR, NN_COEF_VELOCITY = 0, 1
-NN_SOLVER_GPCG, NN_SOLVER_LBFGS = 0, 1
+NN_SOLVER_GPCG, NN_SOLVER_LBFGS, NN_SOLVER_TRON = 0, 1, 2
 NN_PREC_FP64, NN_PREC_MIXED = 0, 1
 NN_FMT_SELL, NN_FMT_CSR = 0, 1
 
@@ -69,7 +69,7 @@ class nn_system_desc(ctypes.Structure):
 class nn_solve_opts(ctypes.Structure):
     _fields_ = [("solver", c_int), ("precision", c_int), ("format", c_int), ("rtol", c_double),
                 ("max_iter", c_int64), ("lbfgs_m", c_int), ("grid_blocks", c_int), ("wait_timeout_s", c_double),
-                ("inner_rtol", c_double), ("extrapolate", c_int)]
+                ("inner_rtol", c_double), ("extrapolate", c_int), ("ksp_rtol", c_double)]
 
 
 class nn_solve_info(ctypes.Structure):

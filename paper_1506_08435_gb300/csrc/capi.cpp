@@ -77,7 +77,7 @@ nn_status check_opts(const nn_solve_opts *o) {
         set_error("solve options are NULL");
         return NN_ERR_INVALID_ARG;
     }
-    if (o->solver != NN_SOLVER_GPCG && o->solver != NN_SOLVER_LBFGS) {
+    if (o->solver != NN_SOLVER_GPCG && o->solver != NN_SOLVER_LBFGS && o->solver != NN_SOLVER_TRON) {
         set_error("unknown solver %d", o->solver);
         return NN_ERR_INVALID_ARG;
     }
@@ -90,9 +90,10 @@ nn_status check_opts(const nn_solve_opts *o) {
         return NN_ERR_INVALID_ARG;
     }
     if (!(o->rtol > 0.0) || o->max_iter < 1 || !(o->wait_timeout_s > 0.0) || o->lbfgs_m < 1 || o->lbfgs_m > 16 ||
-        !(o->inner_rtol > 0.0 && o->inner_rtol < 1.0) || (o->extrapolate < 0 || o->extrapolate > 2)) {
+        !(o->inner_rtol > 0.0 && o->inner_rtol < 1.0) || (o->extrapolate < 0 || o->extrapolate > 2) ||
+        !(o->ksp_rtol > 0.0 && o->ksp_rtol < 1.0)) {
         set_error("invalid solve options (rtol > 0, max_iter >= 1, timeout > 0, 1 <= lbfgs_m <= 16, "
-                  "0 < inner_rtol < 1, 0 <= extrapolate <= 2)");
+                  "0 < inner_rtol < 1, 0 <= extrapolate <= 2, 0 < ksp_rtol < 1)");
         return NN_ERR_INVALID_ARG;
     }
     return NN_OK;
@@ -231,6 +232,7 @@ void nn_solve_opts_default(nn_solve_opts *o) {
     o->wait_timeout_s = 5.0;
     o->inner_rtol = 1e-4;
     o->extrapolate = 2;
+    o->ksp_rtol = 1e-1;
 }
 
 static nn_status solve_common(nn_system *s, const nn_solve_opts *o, int want_transient, int nsteps,

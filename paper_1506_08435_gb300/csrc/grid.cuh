@@ -55,6 +55,8 @@ struct GridArgs {
     double *S, *Y;          // (m+1) slots of n doubles each
     int m;
     double h0;
+    // TRON: relative tolerance of each subspace CG
+    double ksp_rtol;
     // transient: initial iterate of step n+1 (option extrapolate): 1 = the box
     // projection of the linear extrapolation 2 c^(n) - c^(n-1), 2 = of the
     // quadratic one 3 c^(n) - 3 c^(n-1) + c^(n-2); 0 = c^(n)

@@ -1,6 +1,6 @@
 // Single-system solves, host side: scratch, grid sizing and the cooperative
 // launch of the persistent solve kernels (grid.cuh), the projected L-BFGS
-// driver kernel, the FP64 KKT measure and the stand-alone products.
+// and TRON driver kernels, the FP64 KKT measure and the stand-alone products.
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -10,6 +10,7 @@
 #include "internal.h"
 #include "grid.cuh"
 #include "lbfgs.cuh"
+#include "tron.cuh"
 
 namespace nnqp {
 
@@ -47,6 +48,47 @@ __global__ void __launch_bounds__(kSolveThreads) k_lbfgs_grid(GridArgs a) {
         cnt[6] = ls.vec;
         cnt[10] = ls.resets;
         if (!step_outputs(T, R, a, x0, step, nsteps, status, cnt, ls.gp2, den)) return;
+    }
+}
+
+// The same driver with the trust-region Newton solver (FP64, SELL).
+__global__ void __launch_bounds__(kSolveThreads, 2) k_tron_grid(GridArgs a) {
+    __shared__ RedSmem sm;
+    GridTeam T{a.bar, a.partials, (int)gridDim.x + a.bar_extra, a.timeout_ns, 0, 0, &sm};
+    const Rows R = rows_of_block(a.n, a.nslices, blockIdx.x, gridDim.x);
+    double *x0 = a.v64[0];
+    R.each([&](int64_t i) { x0[i] = a.c_in[a.free_node[i]]; });
+    if (!T.sync()) return;
+    const int nsteps = a.mode == MODE_TRANSIENT ? a.nsteps : 1;
+    const Bounds<double> B{a.lo, a.hi, nullptr, nullptr};
+    for (int step = 0; step < nsteps; ++step) {
+        int64_t cnt[kCounters] = {0};
+        double den = a.b0norm;
+        double *b = const_cast<double *>(a.b0);
+        if (a.mode == MODE_TRANSIENT) {
+            if (!transient_rhs(T, R, a, x0, b, den)) return;
+            transient_predict<GridTeam>(R, a, x0, step);
+            cnt[1] += 1;
+            cnt[12] += 4;
+        }
+        if (!(den > 0.0)) den = a.den_fallback;
+        TronVecs v{x0, a.v64[1], a.v64[7], a.v64[8], a.v64[2], a.v64[3], a.v64[4], a.v64[5], a.v64[6],
+                   a.v64[10], b, a.dinv64, a.fmask};
+        const TronCtl c{a.rtol * den, 0.5 * a.rtol * den, a.ksp_rtol, a.ctl.max_spmv, 50};
+        TronStats ts;
+        const int status = tron_solve(T, R, a.A, B, v, c, ts);
+        if (status == ST_TIMEOUT) return;
+        if (v.x != x0) {
+            const double *xs = v.x;
+            R.each([&](int64_t i) { x0[i] = xs[i]; });
+            if (!T.sync()) return;
+        }
+        cnt[1] += ts.spmv;
+        cnt[3] = ts.cg;
+        cnt[4] = ts.iters;
+        cnt[6] = ts.vec;
+        cnt[12] += ts.fl;
+        if (!step_outputs(T, R, a, x0, step, nsteps, status, cnt, ts.gp2, den)) return;
     }
 }
 
@@ -318,10 +360,12 @@ nn_status plan_build(nn_system *s, const nn_solve_opts *o, int mode, int nsteps,
     a.timeout_ns = (unsigned long long)(o->wait_timeout_s * 1e9);
     // grid
     const bool lbfgs = o->solver == NN_SOLVER_LBFGS;
-    if (lbfgs && (mixed || fmt == NN_FMT_CSR)) {
-        set_error("the projected L-BFGS solver runs in FP64 on the SELL format");
+    const bool tron = o->solver == NN_SOLVER_TRON;
+    if ((lbfgs || tron) && (mixed || fmt == NN_FMT_CSR)) {
+        set_error("the projected L-BFGS and TRON solvers run in FP64 on the SELL format");
         return NN_ERR_INVALID_ARG;
     }
+    a.ksp_rtol = o->ksp_rtol;
     if (lbfgs) {
         a.m = std::min(o->lbfgs_m, kLbMaxM);
         a.h0 = 1.0 / s->anorm_inf;
@@ -339,14 +383,16 @@ nn_status plan_build(nn_system *s, const nn_solve_opts *o, int mode, int nsteps,
     const int sms = device_sms();
     const int64_t slices = s->A64.nslices;
     int tpb = kSolveThreads;
-    if (!lbfgs && slices <= (int64_t)4 * 8 * sms && slices > (int64_t)8 * sms / 2) tpb = 512;
+    const bool driver = lbfgs || tron;   // solvers with a kernel of their own
+    if (!driver && slices <= (int64_t)4 * 8 * sms && slices > (int64_t)8 * sms / 2) tpb = 512;
     if (const char *e = getenv("NNQP_GRID_THREADS")) tpb = atoi(e);
-    GridKernel kern = lbfgs ? k_lbfgs_grid : grid_kernel(mode, fmt, a.ctl.cg_variant, tpb);
-    if (!kern && !lbfgs && tpb != kSolveThreads) {
+    GridKernel kern = lbfgs ? k_lbfgs_grid : tron ? k_tron_grid : grid_kernel(mode, fmt, a.ctl.cg_variant, tpb);
+    if (!kern && !driver && tpb != kSolveThreads) {
         tpb = kSolveThreads;
         kern = grid_kernel(mode, fmt, a.ctl.cg_variant, tpb);
     }
     if (lbfgs) tpb = kLbfgsThreads;
+    if (tron) tpb = kSolveThreads;
     if (!kern) {
         set_error("CG variant %d is not available for this mode and format", a.ctl.cg_variant);
         return NN_ERR_INVALID_ARG;
@@ -368,7 +414,7 @@ nn_status plan_build(nn_system *s, const nn_solve_opts *o, int mode, int nsteps,
     // inner products in shared memory when they fit (one block per SM).
     size_t dyn_smem = 0;
     const char *sm_env = getenv("NNQP_SMEM_OP");
-    if (!lbfgs && fmt == NN_FMT_SELL && tpb == 512 && !(sm_env && sm_env[0] == '0')) {
+    if (!driver && fmt == NN_FMT_SELL && tpb == 512 && !(sm_env && sm_env[0] == '0')) {
         if (s->sptr_host.empty()) {
             s->sptr_host.resize((size_t)slices + 1);
             NN_CUDA_TRY(cudaMemcpyAsync(s->sptr_host.data(), s->A64.sptr, sizeof(int64_t) * (slices + 1),

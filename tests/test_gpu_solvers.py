@@ -82,6 +82,81 @@ def test_lbfgs_transient_matches_gpcg():
             compare_solution(outs[solver][n][red.free], ref[n][red.free], red.A, b, spec.lo, spec.hi)
 
 
+# ------------------------------------------------------------------ TRON
+
+TRON_SPECS = {
+    "steady2d_n30": lambda: I.config1_steady_2d(n=30),
+    "steady3d_rot_n12": lambda: I.config3_steady_3d(n=12, seed=5),
+    "cube_hole_mirrored_m2": lambda: I.cube_with_hole(2),
+}
+
+
+@pytest.mark.parametrize("ksp", [1e-1, 1e-3])
+@pytest.mark.parametrize("name", list(TRON_SPECS))
+def test_tron_steady_matches_oracle(name, ksp):
+    """TRON with the paper's loosest and tightest subspace tolerances reaches
+    the oracle's minimiser (the tolerance changes the path, not the result)."""
+    spec = TRON_SPECS[name]()
+    s = gpu_system(spec)
+    c = torch.zeros(spec.n_nodes, dtype=torch.float64, device=DEV)
+    info = P.nn_qp_solve(s, c, P.solve_opts(solver=P.NN_SOLVER_TRON, ksp_rtol=ksp, rtol=1e-11))
+    assert info["status"] == 0, info
+    assert info["iterations"] >= 1 and info["cg_iters"] >= 1
+    red, b, x_ref, _ = oracle_solution(spec)
+    compare_solution(c.cpu().numpy()[red.free], x_ref, red.A, b, spec.lo, spec.hi)
+
+
+@pytest.mark.parametrize("case", ["2d_n4_box", "3d_n3_lower"])
+def test_tron_matches_bruteforce(case):
+    if case == "2d_n4_box":
+        spec = I.tiny_2d(4, 4, hi=1.5e-5)
+    else:
+        Q = I.quaternion_rotation(I.SplitMix64(2, 0))
+        Dm = Q @ np.diag([1000.0, 1.0, 1.0]) @ Q.T
+        spec = I.tiny_3d(3, [Dm[0, 0], Dm[0, 1], Dm[0, 2], Dm[1, 1], Dm[1, 2], Dm[2, 2]])
+    asm, red = oracle_reduced(spec)
+    b = red.rhs()
+    (xb, assign), = O.brute_force(red.A, b, spec.lo, spec.hi)
+    s = gpu_system(spec)
+    c = torch.zeros(spec.n_nodes, dtype=torch.float64, device=DEV)
+    info = P.nn_qp_solve(s, c, P.solve_opts(solver=P.NN_SOLVER_TRON, rtol=1e-12))
+    x = c.cpu().numpy()[red.free]
+    assert info["status"] == 0
+    active = np.where(x == spec.lo, 1, np.where(x == spec.hi, 2, 0))
+    assert np.array_equal(active, assign)
+    assert np.abs(x - xb).max() <= 1e-9 * np.abs(xb).max()
+
+
+def test_tron_transient_matches_oracle():
+    spec = I.config2_transient_3d(n=10, nsteps=5)
+    s = gpu_system(spec)
+    c0 = torch.tensor(spec.c0, device=DEV)
+    cf = torch.zeros_like(c0)
+    hist = torch.zeros(spec.nsteps * spec.n_nodes, dtype=torch.float64, device=DEV)
+    infos = P.nn_transient(s, c0, spec.nsteps, cf, hist, P.solve_opts(solver=P.NN_SOLVER_TRON, rtol=1e-11))
+    assert all(i["status"] == 0 for i in infos)
+    H = hist.cpu().numpy().reshape(spec.nsteps, -1)
+    asm, red = oracle_reduced(spec)
+    ref = O.transient(red, spec.c0, spec.lo, spec.hi, spec.nsteps)
+    for n in range(spec.nsteps):
+        b = red.rhs(ref[n - 1] if n else spec.c0)
+        compare_solution(H[n][red.free], ref[n][red.free], red.A, b, spec.lo, spec.hi)
+
+
+def test_tron_rejects_unsupported_options():
+    spec = I.config1_steady_2d(n=10)
+    s = gpu_system(spec)
+    c = torch.zeros(spec.n_nodes, dtype=torch.float64, device=DEV)
+    for kw in (dict(precision=P.NN_PREC_MIXED), dict(format=P.NN_FMT_CSR), dict(ksp_rtol=0.0),
+               dict(ksp_rtol=1.0)):
+        with pytest.raises(P.NnError) as e:
+            P.nn_qp_solve(s, c, P.solve_opts(solver=P.NN_SOLVER_TRON, **kw))
+        assert e.value.status == P.NN_ERR_INVALID_ARG
+    with pytest.raises(P.NnError) as e:
+        P.nn_batch_solve([s], [c], P.solve_opts(solver=P.NN_SOLVER_TRON))
+    assert e.value.status == P.NN_ERR_INVALID_ARG
+
+
 # ------------------------------------------------------------------ batched persistent solve
 
 def _batch(count=24, nmin=12, nmax=40):

@@ -11,13 +11,21 @@ persistent launch (every QP to KKT <= 1e-10 relative, tighter than the
 1e-8 acceptance).  metric: QP solves per second (50 per step).  The inputs
 (about 12 MB) fit in L2, so L2 is flushed between timed steps (256 MB write).
 
+Options of the default workload: --precision fp64|mixed, --solver
+gpcg|lbfgs|tron (--ksp-rtol: TRON's subspace tolerance), --mass
+consistent|lumped (capacity matrix).
+
 Other workloads (--workload), each printing its own line:
-  steady3d  config 3 (150^3 x 6 tets; --n to shrink), --precision fp64|mixed,
-            --solver gpcg|lbfgs; a step = assembly + one solve
-  steady2d  config 1 (50 x 50, 2D); a step = assembly + one solve
-  batch     config 4 (512 2D instances, one persistent launch); a step =
-            one batched solve of all instances, --precision fp64|mixed
-  serve     config 5 (Poisson arrivals); reports p50/p99 latency
+  steady3d   config 3 (150^3 x 6 tets; --n to shrink), --precision fp64|mixed,
+             --solver gpcg|lbfgs|tron; a step = assembly + one solve
+  steady2d   config 1 (50 x 50, 2D); a step = assembly + one solve
+  batch      config 4 (512 2D instances, one persistent launch); a step =
+             one batched solve of all instances, --precision fp64|mixed; also
+             reports the single-system FP64 solver on the same instances
+  cube_hole  the cube with a cubic hole (Sec. 5.1 analogue; --m, --mesh
+             kuhn|mirrored); a step = assembly + one solve; also reports the
+             Galerkin solution's departure from [0, 1] (an unbounded solve)
+  serve      config 5 (Poisson arrivals); reports p50/p99 latency
 """
 from __future__ import annotations
 

@@ -91,6 +91,45 @@ def test_inputs_are_deterministic_and_shaped_like_the_workloads():
     assert 1800 < len(t) < 2200 and all(np.diff(t) > 0)
 
 
+def test_cube_with_hole_inputs():
+    """Node and element counts of the explicit mesh, the Dirichlet sets (outer
+    faces 0, hole faces 1) and the mirror x -> 1 - x of the second mesh type."""
+    for m in (1, 2, 3):
+        n = 9 * m
+        k = I.cube_with_hole(m, "kuhn")
+        assert k.n_nodes == (n + 1) ** 3 - (m - 1) ** 3
+        assert k.n_elems == 6 * (n ** 3 - m ** 3)
+        assert k.conn.min() == 0 and k.conn.max() == k.n_nodes - 1
+        hole_nodes = (m + 1) ** 3 - (m - 1) ** 3
+        outer_nodes = (n + 1) ** 3 - (n - 1) ** 3
+        assert int(k.dmask.sum()) == hole_nodes + outer_nodes
+        assert int((k.dval == 1.0).sum()) == hole_nodes
+        r = I.cube_with_hole(m, "mirrored")
+        assert np.array_equal(r.conn, k.conn) and np.array_equal(r.dmask, k.dmask)
+        i = np.rint(k.coords[:, 0] * n)
+        assert np.array_equal(r.coords[:, 0], (n - i) / n)     # the lattice point, rounded once
+        assert np.array_equal(r.coords[:, 1:], k.coords[:, 1:])
+    with pytest.raises(ValueError):
+        I.cube_with_hole(1, "other")
+
+
+def test_reference_arm_prints_the_contract_line():
+    """bench.py --impl reference times the oracle (CPU, no GPU needed) on the
+    default workload and prints one JSON line with the contract's keys and
+    the same config as the GPU arm."""
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                          "--warmup", "0"], capture_output=True, text=True, timeout=600,
+                         env=dict(os.environ, CUDA_VISIBLE_DEVICES=""))
+    assert out.returncode == 0, out.stderr[-800:]
+    import json
+    line = json.loads(out.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["metric"] == "QP solves/s" and line["value"] > 0
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
+    assert line["config"]["workload"] == "transient3d_n40_dt0.01_50steps"
+    assert line["config"]["mass"] == "consistent" and line["config"]["solver"] == "gpcg"
+
+
 WORKER = r'''
 import os, sys, json
 sys.path.insert(0, sys.argv[1])

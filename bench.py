@@ -531,7 +531,27 @@ def run_serve(P, torch, args, rank):
         ok += info is not None and info["status"] == 0
     P.nn_serve_destroy(sv)
     launches = P.kernel_launches() - l0
-    return dict(stats=st, wall=wall, offered=len(arrivals), ok=ok, failed=len(failed),
+    # the plain path for comparison: the first requests of the pool, each
+    # assembled and solved alone in FP64 (nn_assemble + nn_qp_solve), one after another
+    dev = torch.device("cuda")
+    seq_n = min(args.pool, 32)
+    fp64 = P.solve_opts(precision=P.NN_PREC_FP64)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    for sp in pool[:seq_n]:
+        s_ = P.nn_assemble(P.Problem(sp, device=dev))
+        c_ = torch.zeros(sp.n_nodes, dtype=torch.float64, device=dev)
+        P.nn_qp_solve(s_, c_, fp64)
+        c_.cpu()
+        del s_
+    seq_s = time.perf_counter() - t1
+    served_work = sum(pool[k].n_nodes for _, k in ids) / max(len(ids), 1)
+    sequential = {"value": seq_n / seq_s, "unit": "solves/s", "requests": seq_n,
+                  "mean_nodes": float(np.mean([sp.n_nodes for sp in pool[:seq_n]])),
+                  "served_mean_nodes": served_work,
+                  "how": "first %d requests of the payload pool, copied from host, assembled and solved alone in "
+                         "FP64 one after another" % seq_n}
+    return dict(stats=st, wall=wall, offered=len(arrivals), ok=ok, failed=len(failed), sequential=sequential,
                 first_failure=failed[0] if failed else None, launches=launches,
                 config={"workload": "serve_poisson%g_for%gs" % (rate, duration), "payload_pool": args.pool,
                         "max_inflight": args.inflight, "queue_capacity": args.queue, "budget_gb": args.budget_gb,
@@ -616,7 +636,8 @@ def main():
                               "bytes_peak": st["bytes_peak"], "inflight_peak": st["inflight_peak"],
                               "higher_is_better": False, "n_gpus": ws,
                               "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
-                              "gpu_launches": r["launches"], "config": r["config"]}))
+                              "gpu_launches": r["launches"], "sequential_fp64": r["sequential"],
+                              "config": r["config"]}))
         return 0
     if args.workload == "transient3d":
         r = run_transient(P, torch, args, rank)

@@ -241,6 +241,40 @@ def timed_steps(torch, step, steps, flush, clk):
 
 # ---------------------------------------------------------------- workloads
 
+def profile_traffic(pdir, kname, workload, precision, digest, scale_from=None, products=None, nnz_free=None):
+    """DRAM bytes per launch of kernel kname on this workload from the committed
+    ncu summary <kname>_<workload>_<precision>.md in pdir (its line
+    "dram_bytes_per_launch: N"), used only while its "source_digest:" line
+    equals digest.  Without a summary for the workload itself, the summary of
+    the smaller case scale_from is scaled by products x nnz_free (its
+    "products_per_launch:" and "nnz_free:" lines).  Returns (bytes or None,
+    where the figure came from or why there is none)."""
+    tfile = os.path.join(pdir, "%s_%s_%s.md" % (kname, workload, precision))
+    scaled = False
+    if not os.path.exists(tfile) and scale_from:
+        tfile = os.path.join(pdir, "%s_%s_%s.md" % (kname, scale_from, precision))
+        scaled = True
+    if not os.path.exists(tfile):
+        return None, "no ncu summary for this workload"
+    name = os.path.basename(tfile)
+    fields = {}
+    for line in open(tfile):
+        key = line.split(":", 1)[0].strip() if ":" in line else ""
+        if key in ("dram_bytes_per_launch", "source_digest", "products_per_launch", "nnz_free"):
+            v = line.split(":", 1)[1].strip()
+            fields[key] = v.split()[0] if v else ""
+    if fields.get("source_digest") != digest:
+        return None, "kernel changed since the ncu capture in %s" % name
+    try:
+        traffic = float(fields["dram_bytes_per_launch"])
+        if not scaled:
+            return traffic, "ncu capture, %s" % name
+        traffic *= products / float(fields["products_per_launch"]) * nnz_free / float(fields["nnz_free"])
+        return traffic, "ncu capture of a smaller case (%s), scaled by products x nnz_free" % name
+    except (KeyError, ValueError, TypeError, ZeroDivisionError):
+        return None, "incomplete ncu summary %s" % name
+
+
 def solver_code(P, args):
     return {"gpcg": P.NN_SOLVER_GPCG, "lbfgs": P.NN_SOLVER_LBFGS, "tron": P.NN_SOLVER_TRON}[args.solver]
 
@@ -660,33 +694,10 @@ def main():
     # summary of this workload and precision (a line "dram_bytes_per_launch:
     # N"), used only while that summary's "source_digest:" line matches the
     # kernel sources as they are now (counters of an older kernel are void)
-    traffic, traffic_src = None, "no ncu summary for this workload"
-    kname = r.get("kernel_name", "k_solve_grid")
-    tfile = os.path.join(ROOT, "profiles", "%s_%s_%s.md" % (kname, r["config"]["workload"], args.precision))
-    scaled = False
-    if not os.path.exists(tfile) and r.get("profile_scale_from"):
-        tfile = os.path.join(ROOT, "profiles", "%s_%s_%s.md" % (kname, r["profile_scale_from"], args.precision))
-        scaled = True
-    if os.path.exists(tfile):
-        fields = {}
-        for line in open(tfile):
-            key = line.split(":", 1)[0].strip() if ":" in line else ""
-            if key in ("dram_bytes_per_launch", "source_digest", "products_per_launch", "nnz_free"):
-                v = line.split(":", 1)[1].strip()
-                fields[key] = v.split()[0] if v else ""
-        if fields.get("source_digest") != source_digest():
-            traffic_src = "kernel changed since the ncu capture in %s" % os.path.basename(tfile)
-        else:
-            try:
-                traffic = float(fields["dram_bytes_per_launch"])
-                traffic_src = "ncu capture, %s" % os.path.basename(tfile)
-                if scaled:
-                    spl = sum(i["spmv"] for i in r["infos"]) / args.steps
-                    traffic *= spl / float(fields["products_per_launch"]) * r["nnz_free"] / float(fields["nnz_free"])
-                    traffic_src = ("ncu capture of a smaller case (%s), scaled by products x nnz_free"
-                                   % os.path.basename(tfile))
-            except (KeyError, ValueError, TypeError):
-                traffic, traffic_src = None, "incomplete ncu summary %s" % os.path.basename(tfile)
+    spl = sum(i["spmv"] for i in r["infos"]) / args.steps
+    traffic, traffic_src = profile_traffic(os.path.join(ROOT, "profiles"), r.get("kernel_name", "k_solve_grid"),
+                                           r["config"]["workload"], args.precision, source_digest(),
+                                           r.get("profile_scale_from"), spl, r.get("nnz_free"))
     infos = r["infos"]
     line = {"metric": r["metric"], "value": value, "unit": r["unit"], "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,

@@ -130,6 +130,25 @@ def test_reference_arm_prints_the_contract_line():
     assert line["config"]["mass"] == "consistent" and line["config"]["solver"] == "gpcg"
 
 
+def test_profile_traffic_lookup(tmp_path):
+    """The bench takes DRAM traffic from a committed ncu summary only while its
+    source digest matches, scales a smaller capture by products x nnz_free,
+    and otherwise reports null with the reason."""
+    sys.path.insert(0, ROOT)
+    import bench
+    (tmp_path / "k_w_fp64.md").write_text("source_digest: abc\ndram_bytes_per_launch: 1000\n")
+    (tmp_path / "k_small_fp64.md").write_text("source_digest: abc\nproducts_per_launch: 10\nnnz_free: 50\n"
+                                              "dram_bytes_per_launch: 2000\n")
+    assert bench.profile_traffic(str(tmp_path), "k", "w", "fp64", "abc")[0] == 1000.0
+    t, why = bench.profile_traffic(str(tmp_path), "k", "w", "fp64", "xyz")
+    assert t is None and "changed" in why
+    t, why = bench.profile_traffic(str(tmp_path), "k", "big", "fp64", "abc", "small", 30, 100)
+    assert t == 2000.0 * 3 * 2 and "scaled" in why
+    assert bench.profile_traffic(str(tmp_path), "k", "other", "fp64", "abc")[0] is None
+    (tmp_path / "k_bad_fp64.md").write_text("source_digest: abc\n")
+    assert "incomplete" in bench.profile_traffic(str(tmp_path), "k", "bad", "fp64", "abc")[1]
+
+
 WORKER = r'''
 import os, sys, json
 sys.path.insert(0, sys.argv[1])

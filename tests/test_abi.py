@@ -61,3 +61,40 @@ def test_struct_layouts_match_the_header(tmp_path):
     sizes = [int(v) for v in subprocess.check_output([str(exe)]).split()]
     for s, n in zip(structs, sizes):
         assert ctypes.sizeof(getattr(P.binding, s)) == n, s
+
+
+def test_assembly_host_validation_without_a_device():
+    """Arguments that nn_assemble rejects on the host, before any device call:
+    each returns its documented status and a message."""
+    import math
+    import nn_inputs as I
+    spec = I.config1_steady_2d(n=4)
+
+    def status_of(mutate=None, opts=None):
+        pr = P.Problem(spec)
+        if mutate:
+            mutate(pr.c)
+        with pytest.raises(P.NnError) as e:
+            P.nn_assemble(pr, opts)
+        assert "nn_assemble" in str(e.value)
+        return e.value.status
+
+    def setf(**kw):
+        return lambda c: [setattr(c, k, v) for k, v in kw.items()]
+
+    assert status_of(setf(dim=4)) == P.NN_ERR_INVALID_ARG
+    assert status_of(setf(memory=7)) == P.NN_ERR_INVALID_ARG
+    assert status_of(setf(lo=1.0, hi=0.0)) == P.NN_ERR_INFEASIBLE
+    assert status_of(setf(lo=math.nan)) == P.NN_ERR_INFEASIBLE
+    assert status_of(setf(dt=-1.0)) == P.NN_ERR_INVALID_ARG
+    assert status_of(setf(dt=math.inf)) == P.NN_ERR_INVALID_ARG
+    assert status_of(setf(coef_kind=9)) == P.NN_ERR_INVALID_ARG
+    assert status_of(setf(coef=None)) == P.NN_ERR_INVALID_ARG
+    assert status_of(setf(nx=0)) == P.NN_ERR_INVALID_ARG
+    assert status_of(opts=P.assemble_opts(lumped_mass=2)) == P.NN_ERR_INVALID_ARG
+    ex = I.cube_with_hole(1)
+    pr = P.Problem(ex)
+    pr.c.n_elems = 0
+    with pytest.raises(P.NnError) as e:
+        P.nn_assemble(pr)
+    assert e.value.status == P.NN_ERR_INVALID_ARG

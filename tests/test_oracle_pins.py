@@ -352,6 +352,18 @@ def test_pgs_and_mprgp_agree(which):
     assert k1["kkt_rel"] < 1e-12 and k1["bounds_ok"]
 
 
+def test_pgs_and_mprgp_agree_on_the_mirrored_cube_with_a_hole():
+    """Explicit mesh with a hole and active bounds: the two independent
+    solvers reach the same minimiser, with lower bounds active."""
+    sp, asm, red = _cube_hole(1, "mirrored")
+    b = red.rhs()
+    x1, _ = O.solve_qp(red.A, b, 0.0, 1.0)
+    x2, _ = O.pgs(red.A, b, 0.0, 1.0, tol=1e-16, maxsweep=400000)
+    assert O.kkt(red.A, b, 0.0, 1.0, x2)["kkt_rel"] < 1e-9
+    assert np.abs(x1 - x2).max() <= 1e-8 * np.abs(x1).max()
+    assert (x1 == 0.0).sum() > 0
+
+
 # ------------------------------------------------------------------ closed-form QPs
 
 def test_diagonal_qp_closed_form():

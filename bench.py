@@ -604,7 +604,7 @@ def main():
     ap.add_argument("--mass", default="consistent", choices=["consistent", "lumped"],
                     help="capacity matrix of the transient workload")
     ap.add_argument("--solver", default="gpcg", choices=["gpcg", "lbfgs", "tron"])
-    ap.add_argument("--ksp-rtol", type=float, default=1e-1, help="TRON: relative tolerance of each subspace CG")
+    ap.add_argument("--ksp-rtol", type=float, default=1e-1, help="TRON: subspace tolerance relative to the face gradient at the Cauchy point")
     ap.add_argument("--n", type=int, default=0)
     ap.add_argument("--m", type=int, default=16, help="cube with a hole: n = 9m hexahedra per side")
     ap.add_argument("--mesh", default="mirrored", choices=["kuhn", "mirrored"], help="cube with a hole: mesh type")

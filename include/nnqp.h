@@ -189,7 +189,8 @@ typedef struct {
                             0 = c^(n); 1 = box projection of 2 c^(n) - c^(n-1);
                             2 (default) = box projection of 3 c^(n) - 3 c^(n-1) + c^(n-2)
                             (measured on the 40^3 run: 6,853 / 5,817 / 5,356 products) */
-    double ksp_rtol;     /* TRON: each subspace CG stops at ||r|| <= ksp_rtol ||r_0||
+    double ksp_rtol;     /* TRON: the subspace steps of an iteration stop once the free-face
+                            gradient is at most ksp_rtol times its value at the Cauchy point
                             (default 1e-1; the paper's TRON1/2/3 use 1e-1, 1e-2, 1e-3) */
 } nn_solve_opts;
 

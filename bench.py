@@ -1,31 +1,45 @@
 """Benchmark of the non-negative diffusion QP path on GB300.
 
-Default workload (no flags, N = 1): the 3D transient problem -- unit cube,
-40^3 hexahedra x 6 tetrahedra (68,921 nodes), dispersion tensor from the
-vortex velocity field (alpha_L = 1, alpha_T = 1e-3, D_M = 1e-9), c = 1 on
-the x = 0 patch and c = 0 on x = 1, 0 <= c <= 1, backward Euler dt = 0.01
-over 50 steps, one warm-started QP per step, FP64.  One benchmark step is
-the whole path on one synthetic input: device assembly (pattern, element
-matrices, elimination, SELL build) + the 50-step transient run in one
-persistent launch (every QP to KKT <= 1e-10 relative, tighter than the
-1e-8 acceptance).  metric: QP solves per second (50 per step).  The inputs
-(about 12 MB) fit in L2, so L2 is flushed between timed steps (256 MB write).
+Default workload (no flags, N = 1): the 3D steady problem of 150^3
+hexahedra x 6 tetrahedra (3,442,951 nodes, 3,414,525 free unknowns, about
+50.7M nonzeros in the reduced matrix), dispersion tensor from the vortex
+velocity field rotated per 10^3 block of hexahedra (seed 1506; alpha_L = 1,
+alpha_T = 1e-3, D_M = 1e-9), c = 1 on the x = 0 patch and c = 0 on x = 1,
+0 <= c <= 1.  One benchmark step is the whole path on one synthetic input:
+device assembly (pattern, element matrices, elimination, SELL build) + one
+QP solve to KKT <= 1e-10 relative (tighter than the 1e-8 acceptance) in one
+persistent launch.  metric: QP solves per second.  The line is the plain
+FP64 solve; its "mixed" object is the same workload solved with FP32 operator
+values and FP32 inner solves refined in FP64 (FP64 residual, KKT and stored
+solution), with "vs_plain_fp64" = mixed solves/s / FP64 solves/s.  Inputs
+(0.6-0.9 GB of operator) are far larger than L2, and L2 is flushed between
+steps anyway (256 MB write).
 
-Options of the default workload: --precision fp64|mixed, --solver
-gpcg|lbfgs|tron (--ksp-rtol: TRON's subspace tolerance), --mass
-consistent|lumped (capacity matrix).
+roofline: achieved = algorithmic bytes of the solve launch (every product
+counted at the paper's MatMult traffic, every vector stream of the fused
+passes at its width) / the launch's CUDA-event time; "dram_gbs" beside it is
+the ncu-measured DRAM bytes of the same launch (scaled from a capture of a
+smaller case, see traffic_source) / the same time; "alu" is the FP64 pipe
+(algorithmic FP64 operations / time against 152 SMs x 2 DFMA/clk x 2 flop x
+2.07 GHz).  "bound" names the larger of the two fractions.
+
+Options: --precision fp64|mixed|both (default both for steady3d),
+--solver gpcg|lbfgs|tron (--ksp-rtol: TRON's subspace tolerance), --n to
+shrink the grid, --e2e-steps (end-to-end repeats, default 5).
 
 Other workloads (--workload), each printing its own line:
-  steady3d   config 3 (150^3 x 6 tets; --n to shrink), --precision fp64|mixed,
-             --solver gpcg|lbfgs|tron; a step = assembly + one solve
-  steady2d   config 1 (50 x 50, 2D); a step = assembly + one solve
-  batch      config 4 (512 2D instances, one persistent launch); a step =
-             one batched solve of all instances, --precision fp64|mixed; also
-             reports the single-system FP64 solver on the same instances
-  cube_hole  the cube with a cubic hole (Sec. 5.1 analogue; --m, --mesh
-             kuhn|mirrored); a step = assembly + one solve; also reports the
-             Galerkin solution's departure from [0, 1] (an unbounded solve)
-  serve      config 5 (Poisson arrivals); reports p50/p99 latency
+  transient3d  config 2: 40^3 x 6 tets, dt = 0.01, 50 backward-Euler steps
+               (one warm-started QP per step) in one launch; --mass
+               consistent|lumped; a step = assembly + the 50-step run
+  steady2d     config 1 (50 x 50, 2D); a step = assembly + one solve
+  batch        config 4 (512 2D instances, one persistent launch); a step =
+               one batched solve of all instances, --precision fp64|mixed;
+               also reports the single-system FP64 solver on the same instances
+  cube_hole    the cube with a cubic hole (Sec. 5.1 analogue; --m, --mesh
+               kuhn|mirrored); a step = assembly + one solve; also reports the
+               Galerkin solution's departure from [0, 1] (an unbounded solve)
+  serve        config 5 (Poisson arrivals, request r seeded (2015, r));
+               reports p50/p99 latency
 """
 from __future__ import annotations
 
@@ -135,11 +149,61 @@ class ClockSampler:
 
 # ---------------------------------------------------------------- the oracle baseline (CPU)
 
+class Steady3dOracle:
+    """The FP64 oracle on the steady 3D workload, sampled: the oracle
+    assembles the n^3 system itself (mesh, element loop, elimination; timed
+    once), then runs bounded batches of its MPRGP iterations from the zero
+    start (timed per batch).  A whole oracle solve is
+        t_setup + I * t_iteration,
+    with I the MPRGP iterations the oracle needs for this system, recorded by
+    oracle/record_oracle_runs.py (a full oracle run; its active-set polish,
+    a few percent of the run, is left out, in the oracle's favour)."""
+
+    def __init__(self, n, threads):
+        from oracle import oracle as O
+        self.O, self.n, self.threads = O, n, threads
+        rec = os.path.join(ROOT, "oracle", "runs", "steady3d_n%d.json" % n)
+        self.record = json.load(open(rec)) if os.path.exists(rec) else None
+        spec = I.config3_steady_3d(n=n)
+        t0 = time.perf_counter()
+        coords, conn = O.mesh_structured(3, spec.nx)
+        asm = O.assemble(coords, conn, spec.coef_kind, spec.coef, spec.aL, spec.aT, spec.DM, spec.f_elem)
+        self.red = O.Reduced(asm, spec.dmask, spec.dval)
+        self.b = self.red.rhs()
+        self.t_setup = time.perf_counter() - t0
+        self.spec = spec
+
+    def iterations(self, k):
+        """Seconds per MPRGP iteration over k iterations from the zero start."""
+        t0 = time.perf_counter()
+        self.O.mprgp(self.red.A, self.b, self.spec.lo, self.spec.hi, maxit=k, threads=self.threads)
+        return (time.perf_counter() - t0) / k
+
+    def value(self, t_it):
+        if self.record is None:
+            return None
+        return 1.0 / (self.t_setup + self.record["mprgp_iters"] * t_it)
+
+    def describe(self, k):
+        if self.record is None:
+            return "no record of the oracle's iteration count for steady3d_n%d" % self.n
+        return ("oracle (FP64 C, MPRGP, %d threads) on the %d^3 steady system: its own assembly + elimination "
+                "timed once (%.1f s), %d MPRGP iterations from the zero start timed, whole solve = setup + "
+                "%d iterations (recorded full oracle run, kkt %.1e; polish excluded)"
+                % (self.threads, self.n, self.t_setup, k, self.record["mprgp_iters"], self.record["kkt_rel"]))
+
+
 def oracle_sample(workload, budget_s=20.0, n=None, lumped=False):
     """The FP64 oracle as it stands, on a bounded sample of the workload;
     returns (units per second, cores used, description)."""
     from oracle import oracle as O
     threads = os.cpu_count() or 1
+    if workload == "steady3d":
+        orc = Steady3dOracle(n or 150, threads)
+        t1 = orc.iterations(5)
+        k = max(5, min(2000, int(max(budget_s - orc.t_setup, 5.0) / max(t1, 1e-6))))
+        t_it = orc.iterations(k)
+        return orc.value(t_it), threads, orc.describe(k)
     if workload == "transient3d":
         spec = I.config2_transient_3d()
         coords, conn = O.mesh_structured(3, spec.nx)
@@ -284,7 +348,7 @@ def transient_config(spec, args):
     return {"workload": "transient3d_n40_dt0.01_50steps", "nodes": spec.n_nodes, "tets": spec.n_elems,
             "qp_per_step": spec.nsteps, "rtol": args.rtol, "l2": "flushed between steps (256 MB write)",
             "solver": args.solver + ("(ksp %g)" % args.ksp_rtol if args.solver == "tron" else ""),
-            "precision": args.precision, "mass": args.mass,
+            "precision": getattr(args, "cur_precision", args.precision), "mass": args.mass,
             "first_iterate": "projected 3c^n - 3c^(n-1) + c^(n-2)"}
 
 
@@ -293,7 +357,7 @@ def run_transient(P, torch, args, rank):
     dev = torch.device("cuda")
     nsteps = spec.nsteps
     prob = P.Problem(spec, device=dev)
-    mixed = args.precision == "mixed"
+    mixed = args.cur_precision == "mixed"
     opts = P.solve_opts(rtol=args.rtol, solver=solver_code(P, args), ksp_rtol=args.ksp_rtol,
                         precision=P.NN_PREC_MIXED if mixed else P.NN_PREC_FP64)
     aopts = P.assemble_opts(build_mixed=1 if mixed else 0, lumped_mass=1 if args.mass == "lumped" else 0)
@@ -321,7 +385,7 @@ def run_transient(P, torch, args, rank):
     cfh = torch.zeros_like(c0h).pin_memory()
     stream = torch.cuda.current_stream()
     e2e = []
-    for _ in range(args.steps):
+    for _ in range(min(args.steps, args.e2e_steps)):
         flush.zero_()
         torch.cuda.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -348,7 +412,7 @@ def run_steady(P, torch, args, rank, dim):
     else:
         spec = I.config1_steady_2d(n=args.n or 50)
     dev = torch.device("cuda")
-    prec = P.NN_PREC_MIXED if args.precision == "mixed" else P.NN_PREC_FP64
+    prec = P.NN_PREC_MIXED if args.cur_precision == "mixed" else P.NN_PREC_FP64
     opts = P.solve_opts(rtol=args.rtol, precision=prec, max_iter=args.max_iter,
                         solver=solver_code(P, args), ksp_rtol=args.ksp_rtol)
     aopts = P.assemble_opts(build_mixed=1 if prec == P.NN_PREC_MIXED else 0)
@@ -377,7 +441,7 @@ def run_steady(P, torch, args, rank, dim):
     ch = torch.zeros(spec.n_nodes, dtype=torch.float64).pin_memory()
     stream = torch.cuda.current_stream()
     e2e = []
-    for _ in range(args.steps):
+    for _ in range(min(args.steps, args.e2e_steps)):
         flush.zero_()
         torch.cuda.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -443,10 +507,11 @@ def run_steady(P, torch, args, rank, dim):
                 kern_bytes=[o[0]["bytes_algo"] for o in outs], units_per_step=1, e2e=e2e,
                 nnz_free=desc.get("nnz_free"), profile_scale_from=scale_from,
                 h2d=hbytes + ch.numel() * 8, d2h=ch.numel() * 8, clocks=clocks, launches=launches,
-                config={"workload": name, "nodes": spec.n_nodes, "free": desc.get("n_free"),
-                        "nnz_free": desc.get("nnz_free"), "rtol": args.rtol,
-                        "solver": args.solver + ("(ksp %g)" % args.ksp_rtol if args.solver == "tron" else ""),
-                        "precision": args.precision, "l2": "flushed between steps (256 MB write)"},
+                config=(steady3d_config(spec, args.n or 150, args) if args.workload == "steady3d" else
+                        {"workload": name, "nodes": spec.n_nodes, "free": desc.get("n_free"),
+                         "rtol": args.rtol,
+                         "solver": args.solver + ("(ksp %g)" % args.ksp_rtol if args.solver == "tron" else ""),
+                         "precision": args.cur_precision, "l2": "flushed between steps (256 MB write)"}),
                 dtype="f64" if prec == P.NN_PREC_FP64 else "f32+f64", unit="QP solves/s", metric="QP solves/s")
 
 
@@ -454,7 +519,7 @@ def run_batch(P, torch, args, rank):
     count = args.count
     insts = I.config4_batch(count)
     dev = torch.device("cuda")
-    prec = P.NN_PREC_MIXED if args.precision == "mixed" else P.NN_PREC_FP64
+    prec = P.NN_PREC_MIXED if args.cur_precision == "mixed" else P.NN_PREC_FP64
     systems = [P.nn_assemble(P.Problem(sp, device=dev)) for sp in insts]
     cs = [torch.zeros(sp.n_nodes, dtype=torch.float64, device=dev) for sp in insts]
     opts = P.solve_opts(rtol=args.rtol, precision=prec)
@@ -496,7 +561,7 @@ def run_batch(P, torch, args, rank):
     c0h = [torch.zeros(sp.n_nodes, dtype=torch.float64).pin_memory() for sp in insts]
     outh = [torch.zeros(sp.n_nodes, dtype=torch.float64).pin_memory() for sp in insts]
     e2e = []
-    for _ in range(args.steps):
+    for _ in range(min(args.steps, args.e2e_steps)):
         flush.zero_()
         torch.cuda.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -520,7 +585,7 @@ def run_batch(P, torch, args, rank):
                 sequential_fp64={"value": count / (seq_ms / 1e3), "unit": "QP solves/s", "ms": seq_ms,
                                  "how": "nn_qp_solve per instance, FP64, one after another"},
                 config={"workload": "batch2d_%d" % count, "instances": count, "threads_per_block": tuned // 100, "ctas_per_instance": tuned % 100,
-                        "precision": args.precision, "rtol": args.rtol, "l2": "flushed between steps"},
+                        "precision": args.cur_precision, "rtol": args.rtol, "l2": "flushed between steps"},
                 dtype="f64" if prec == P.NN_PREC_FP64 else "f32+f64", unit="QP solves/s", metric="QP solves/s")
 
 
@@ -598,9 +663,10 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="transient3d",
+    ap.add_argument("--workload", default="steady3d",
                     choices=["transient3d", "steady3d", "steady2d", "batch", "serve", "cube_hole"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--precision", default="auto", choices=["auto", "fp64", "mixed", "both"],
+                    help="auto: both for steady3d (FP64 line + mixed object), fp64 otherwise")
     ap.add_argument("--mass", default="consistent", choices=["consistent", "lumped"],
                     help="capacity matrix of the transient workload")
     ap.add_argument("--solver", default="gpcg", choices=["gpcg", "lbfgs", "tron"])
@@ -617,6 +683,7 @@ def main():
     ap.add_argument("--inflight", type=int, default=8)
     ap.add_argument("--queue", type=int, default=64)
     ap.add_argument("--budget-gb", type=float, default=120.0)
+    ap.add_argument("--e2e-steps", type=int, default=5, help="end-to-end repeats (host buffers, copies timed)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--out-dir", default=os.path.join(ROOT, "bench_out"))
     args = ap.parse_args()
@@ -626,29 +693,15 @@ def main():
     hbm_peak = pk["hbm_gbs"] if pk else FALLBACK_HBM
     peak_src = "measured (MEASURED_PEAKS.json hbm_gbs)" if pk else "fallback"
 
+    if args.workload == "steady3d" and args.precision == "auto":
+        args.precision = "both"
+    elif args.precision == "auto":
+        args.precision = "fp64"
+    if args.precision == "both" and args.workload != "steady3d":
+        args.precision = "fp64"
+
     if args.impl == "reference":
-        if rank != 0:
-            return 0
-        vals, cores, desc = [], os.cpu_count() or 1, ""
-        t0 = time.perf_counter()
-        for _ in range(args.warmup):
-            oracle_sample(args.workload, budget_s=1.0, lumped=args.mass == "lumped")
-        for _ in range(args.steps):
-            v, cores, desc = oracle_sample(args.workload, budget_s=8.0, lumped=args.mass == "lumped")
-            vals.append(v)
-        v = float(np.median(vals))
-        print(json.dumps({"impl": "reference", "metric": "QP solves/s", "value": v, "unit": "QP solves/s",
-                          "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-                          "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-                          "data": "synthetic",
-                          "config": (transient_config(I.config2_transient_3d(), args) if args.workload == "transient3d"
-                                     else {"workload": args.workload}),
-                          "cpu_baseline": {"value": v, "unit": "QP solves/s", "cores": cores, "kind": "oracle",
-                                           "sample": desc},
-                          "e2e": {"value": v, "unit": "QP solves/s", "h2d_bytes_per_step": 0,
-                                  "d2h_bytes_per_step": 0},
-                          "wall_s": time.perf_counter() - t0}))
-        return 0
+        return reference_arm(args, rank)
 
     import torch
     import paper_1506_08435_gb300 as P
@@ -658,32 +711,95 @@ def main():
     P.lib()
     barrier(dist)
     if args.workload == "serve":
-        r = run_serve(P, torch, args, rank)
-        st = r["stats"]
-        if rank == 0:
-            print(json.dumps({"metric": "serving p50/p99 latency", "value": st["p50_ms"], "unit": "ms",
-                              "p99_ms": st["p99_ms"], "mean_ms": st["mean_ms"], "solves_per_s": st["solves_per_s"],
-                              "offered": r["offered"], "offered_per_s": args.rate, "completed": st["completed"],
-                              "ok": r["ok"], "failed": st["failed"], "first_failure": r["first_failure"],
-                              "rejected": st["rejected"],
-                              "wall_s": r["wall"], "saturated": st["rejected"] > 0 or st["solves_per_s"] < 0.95 * args.rate,
-                              "bytes_peak": st["bytes_peak"], "inflight_peak": st["inflight_peak"],
-                              "higher_is_better": False, "n_gpus": ws,
-                              "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
-                              "gpu_launches": r["launches"], "sequential_fp64": r["sequential"],
-                              "config": r["config"]}))
-        return 0
+        return serve_line(P, torch, args, rank, ws)
+    precisions = ["fp64", "mixed"] if args.precision == "both" else [args.precision]
+    lines = []
+    for prec in precisions:
+        args.cur_precision = prec
+        if args.workload == "transient3d":
+            r = run_transient(P, torch, args, rank)
+        elif args.workload in ("steady3d", "cube_hole"):
+            r = run_steady(P, torch, args, rank, 3)
+        elif args.workload == "steady2d":
+            r = run_steady(P, torch, args, rank, 2)
+        else:
+            r = run_batch(P, torch, args, rank)
+        barrier(dist)
+        lines.append(result_line(r, args, prec, dist, ws, hbm_peak, peak_src))
+    line = lines[0]
+    if len(lines) > 1:
+        m = lines[1]
+        sub = {k: m[k] for k in ("value", "unit", "ms_per_step", "dtype", "roofline", "alu", "e2e", "max_kkt_rel",
+                                 "statuses_ok", "spmv_per_step", "spmv64_per_step", "refinements_per_step",
+                                 "fp64_fallbacks", "gpu_launches", "clocks") if k in m}
+        line["mixed"] = sub
+        line["vs_plain_fp64"] = m["value"] / line["value"]
+        line["precision_note"] = "the line is the plain FP64 solve; \"mixed\" is the same workload in mixed precision"
+    if rank == 0 and not args.no_cpu_baseline:
+        v, cores, desc = oracle_sample(args.workload, n=args.n or None, lumped=args.mass == "lumped")
+        if v is not None:
+            line["cpu_baseline"] = {"value": v, "unit": line["unit"], "cores": cores, "kind": "oracle", "sample": desc}
+    if rank == 0:
+        print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def workload_config(args):
+    """config object of a line (both arms print the same one)."""
     if args.workload == "transient3d":
-        r = run_transient(P, torch, args, rank)
-    elif args.workload == "steady3d":
-        r = run_steady(P, torch, args, rank, 3)
-    elif args.workload == "steady2d":
-        r = run_steady(P, torch, args, rank, 2)
-    elif args.workload == "cube_hole":
-        r = run_steady(P, torch, args, rank, 3)
+        return transient_config(I.config2_transient_3d(), args)
+    if args.workload == "steady3d":
+        n = args.n or 150
+        spec = I.config3_steady_3d(n=n)
+        return steady3d_config(spec, n, args)
+    return {"workload": args.workload}
+
+
+def steady3d_config(spec, n, args):
+    return {"workload": "steady3d_n%d" % n, "nodes": int(spec.n_nodes), "tets": 6 * n ** 3,
+            "free": int((np.asarray(spec.dmask) == 0).sum()), "rtol": args.rtol,
+            "solver": args.solver + ("(ksp %g)" % args.ksp_rtol if args.solver == "tron" else ""),
+            "precision": args.precision, "l2": "inputs far larger than L2, flushed between steps (256 MB write)"}
+
+
+def reference_arm(args, rank):
+    """The oracle as it stands on the host cores, on this arm's config,
+    metric and unit; each step a bounded sample of the workload."""
+    if rank != 0:
+        return 0
+    t0 = time.perf_counter()
+    cores = os.cpu_count() or 1
+    if args.workload == "steady3d":
+        orc = Steady3dOracle(args.n or 150, cores)
+        for _ in range(args.warmup):
+            orc.iterations(2)
+        k = 20
+        vals = [orc.value(orc.iterations(k)) for _ in range(args.steps)]
+        desc = orc.describe(k) + "; one step = one batch"
     else:
-        r = run_batch(P, torch, args, rank)
-    barrier(dist)
+        vals = []
+        for _ in range(args.warmup):
+            oracle_sample(args.workload, budget_s=1.0, lumped=args.mass == "lumped")
+        for _ in range(args.steps):
+            v, cores, desc = oracle_sample(args.workload, budget_s=8.0, lumped=args.mass == "lumped")
+            vals.append(v)
+    v = float(np.median(vals)) if all(x is not None for x in vals) else None
+    print(json.dumps({"impl": "reference", "metric": "QP solves/s", "value": v, "unit": "QP solves/s",
+                      "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                      "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                      "data": "synthetic", "config": workload_config(args),
+                      "cpu_baseline": {"value": v, "unit": "QP solves/s", "cores": cores, "kind": "oracle",
+                                       "sample": desc},
+                      "e2e": {"value": v, "unit": "QP solves/s", "h2d_bytes_per_step": 0,
+                              "d2h_bytes_per_step": 0},
+                      "wall_s": time.perf_counter() - t0}))
+    return 0
+
+
+def result_line(r, args, prec, dist, ws, hbm_peak, peak_src):
+    """The contract's JSON line of one timed run r."""
     total_ms = max_over_ranks(dist, sum(r["times"]))
     units = r["units_per_step"] * args.steps * ws
     value = units / (total_ms / 1e3)
@@ -694,51 +810,71 @@ def main():
     # summary of this workload and precision (a line "dram_bytes_per_launch:
     # N"), used only while that summary's "source_digest:" line matches the
     # kernel sources as they are now (counters of an older kernel are void)
-    spl = sum(i["spmv"] for i in r["infos"]) / args.steps
-    traffic, traffic_src = profile_traffic(os.path.join(ROOT, "profiles"), r.get("kernel_name", "k_solve_grid"),
-                                           r["config"]["workload"], args.precision, source_digest(),
-                                           r.get("profile_scale_from"), spl, r.get("nnz_free"))
     infos = r["infos"]
+    spl = sum(i["spmv"] for i in infos) / args.steps
+    traffic, traffic_src = profile_traffic(os.path.join(ROOT, "profiles"), r.get("kernel_name", "k_solve_grid"),
+                                           r["config"]["workload"], prec, source_digest(),
+                                           r.get("profile_scale_from"), spl, r.get("nnz_free"))
+    roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
+            "traffic": traffic, "traffic_source": traffic_src,
+            "kernel": "solve kernel (persistent, one launch per step)", "kernel_ms": kern_ms,
+            "algo_bytes_per_launch": kern_bytes, "peak_source": peak_src,
+            "achieved_is": "algorithmic bytes (products at the MatMult model + every vector stream) / launch time"}
+    if traffic:
+        roof["dram_gbs"] = traffic / (kern_ms / 1e3) / 1e9
+        roof["dram_frac"] = roof["dram_gbs"] / hbm_peak
     line = {"metric": r["metric"], "value": value, "unit": r["unit"], "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": r["dtype"], "data": "synthetic", "config": r["config"],
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                         "frac": achieved / hbm_peak, "traffic": traffic, "traffic_source": traffic_src,
-                         "kernel": "solve kernel (persistent, one launch per step)",
-                         "kernel_ms": kern_ms, "algo_bytes_per_launch": kern_bytes, "peak_source": peak_src},
-            "gpu_launches": r["launches"], "clocks": r["clocks"],
+            "roofline": roof, "gpu_launches": r["launches"], "clocks": r["clocks"],
             "max_kkt_rel": float(max(i["kkt_rel"] for i in infos)),
             "statuses_ok": all(i["status"] == 0 for i in infos),
             "spmv_per_step": sum(i["spmv"] for i in infos) / args.steps,
+            "spmv64_per_step": sum(i["spmv64"] for i in infos) / args.steps,
             "cg_iters_per_step": sum(i["cg_iters"] for i in infos) / args.steps,
-            "phases_per_step": sum(i["iterations"] for i in infos) / args.steps}
-    # the FP64 pipe as a second bound: algorithmic FP64 operations of the dominant
-    # kernel per launch / its time, against 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
+            "phases_per_step": sum(i["iterations"] for i in infos) / args.steps,
+            "refinements_per_step": sum(i["refinements"] for i in infos) / args.steps,
+            "fp64_fallbacks": int(sum(i["fp64_fallback"] for i in infos))}
+    # the FP64 pipe as the second roof: algorithmic FP64 operations of the
+    # launch / its time, against 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
     fl64 = sum(i.get("flops64_algo", 0.0) for i in infos) / args.steps
     if fl64 > 0:
         ach = fl64 / (kern_ms / 1e3) / 1e9
-        line["fp64_pipe"] = {"achieved": ach, "peak": FP64_PIPE_PEAK_GFLOPS, "unit": "GFLOP/s",
-                             "frac": ach / FP64_PIPE_PEAK_GFLOPS, "flops_per_launch": fl64}
-    if r.get("graph"):
-        line["graph"] = r["graph"]
-    if r.get("dmp"):
-        line["galerkin_dmp"] = r["dmp"]
-    if r.get("sequential_fp64"):
-        line["sequential_fp64"] = r["sequential_fp64"]
-    if r["e2e"] is not None:
+        line["alu"] = {"bound": "alu", "pipe": "fp64", "achieved": ach, "peak": FP64_PIPE_PEAK_GFLOPS,
+                       "unit": "GFLOP/s", "frac": ach / FP64_PIPE_PEAK_GFLOPS, "flops_per_launch": fl64,
+                       "peak_source": "152 SMs x 2 DFMA/clk (ncu unit count) x 2 flop x 2.07 GHz"}
+        if line["alu"]["frac"] > max(roof["frac"], roof.get("dram_frac") or 0.0):
+            roof["bound"] = "alu"
+            roof["bound_note"] = "the FP64 pipe fraction (alu) exceeds the HBM fraction"
+    for key in ("graph", "dmp", "sequential_fp64"):
+        if r.get(key):
+            line["galerkin_dmp" if key == "dmp" else key] = r[key]
+    if r["e2e"]:
         e2e_ms = max_over_ranks(dist, sum(r["e2e"]))
         line["e2e"] = {"value": r["units_per_step"] * len(r["e2e"]) * ws / (e2e_ms / 1e3), "unit": r["unit"],
-                       "h2d_bytes_per_step": r["h2d"], "d2h_bytes_per_step": r["d2h"]}
+                       "h2d_bytes_per_step": r["h2d"], "d2h_bytes_per_step": r["d2h"], "steps": len(r["e2e"])}
     else:
         line["e2e"] = None
-    if rank == 0 and not args.no_cpu_baseline:
-        v, cores, desc = oracle_sample(args.workload, lumped=args.mass == "lumped")
-        if v is not None:
-            line["cpu_baseline"] = {"value": v, "unit": r["unit"], "cores": cores, "kind": "oracle", "sample": desc}
+    return line
+
+
+def serve_line(P, torch, args, rank, ws):
+    r = run_serve(P, torch, args, rank)
+    st = r["stats"]
     if rank == 0:
-        print(json.dumps(line))
-    if dist is not None:
-        dist.destroy_process_group()
+        print(json.dumps({"metric": "serving p50/p99 latency", "value": st["p50_ms"], "unit": "ms",
+                          "p99_ms": st["p99_ms"], "mean_ms": st["mean_ms"], "solves_per_s": st["solves_per_s"],
+                          "offered": r["offered"], "offered_per_s": args.rate, "completed": st["completed"],
+                          "ok": r["ok"], "failed": st["failed"], "first_failure": r["first_failure"],
+                          "rejected": st["rejected"], "wall_s": r["wall"],
+                          "saturated": st["rejected"] > 0 or st["solves_per_s"] < 0.95 * args.rate,
+                          "bytes_peak_measured": st["bytes_peak"], "bytes_reserved_peak": st["bytes_reserved_peak"],
+                          "estimate_overruns": st["estimate_overruns"],
+                          "estimate_max_ratio": st["estimate_max_ratio"], "inflight_peak": st["inflight_peak"],
+                          "higher_is_better": False, "n_gpus": ws,
+                          "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
+                          "gpu_launches": r["launches"], "sequential_fp64": r["sequential"],
+                          "config": r["config"]}))
     return 0
 
 

@@ -71,6 +71,10 @@ const char *nn_version(void);
 /* Number of CUDA kernels this library has launched in this process (all
  * devices, all threads); for accounting of device work, never reset. */
 uint64_t nn_kernel_launches(void);
+/* Number of device allocations this library has made in this process (all
+ * devices, all threads: every buffer it takes from its stream-ordered memory
+ * pool); for accounting, never reset. */
+uint64_t nn_device_allocations(void);
 
 /* ------------------------------------------------------------------ mesh */
 
@@ -281,7 +285,7 @@ nn_status nn_kkt_residual(const nn_system *s, const double *c, const double *c_p
 
 /* y = A x on the free unknowns (x, y device [NF]); format NN_FMT_SELL or
  * NN_FMT_CSR; precision NN_PREC_FP64, or NN_PREC_MIXED for the FP32-value
- * operator (x, y still FP64).  Stream-ordered, asynchronous. */
+ * operator (SELL only; x, y still FP64).  Stream-ordered, asynchronous. */
 nn_status nn_spmv(const nn_system *s, const double *x, double *y, int format, int precision, void *stream);
 
 /* y = A x with the FP32-value operator (the product of nn_spmv with
@@ -300,8 +304,12 @@ nn_status nn_spmv(const nn_system *s, const double *x, double *y, int format, in
  *   - Every GPU on which this library is loaded holds that 16 MiB array
  *     until the process exits.
  *   - The first call on each device looks up the array's device address
- *     (cudaGetSymbolAddress) with that device current; make that first call
- *     before any stream capture begins.
+ *     (cudaGetSymbolAddress) with that device current and keeps it for the
+ *     life of the process; make that first call before any stream capture
+ *     begins.  A cudaDeviceReset (or any other teardown of the device's
+ *     primary context) unloads the array and leaves the kept address stale:
+ *     a process that resets a device must not call this entry point on that
+ *     device afterwards.
  *   - All calls share the one array and it keeps the last call's contents
  *     (each call overwrites what it reads, nothing has to start at zero).
  *     Calls whose kernels overlap on the GPU -- on different streams, or
@@ -348,23 +356,38 @@ typedef struct {
     int64_t submitted, completed, failed, rejected;
     double p50_ms, p99_ms, mean_ms;  /* latency submit -> result ready */
     double solves_per_s;             /* completed / (last completion - first submit) */
-    size_t bytes_resident, bytes_peak, budget;
+    size_t bytes_resident;           /* admission estimates of the requests admitted now */
+    size_t bytes_peak;               /* largest sum of MEASURED device bytes over finished requests
+                                        that held memory at the same time (each request's bytes:
+                                        the most of its assembly with temporaries, or its system +
+                                        solution + solve scratch) */
+    size_t budget;
     int64_t inflight_peak;
+    size_t bytes_reserved_peak;      /* largest sum of admission estimates (never above budget) */
+    int64_t estimate_overruns;       /* finished requests whose measured bytes exceeded the estimate */
+    double estimate_max_ratio;       /* largest measured / estimated bytes of a finished request */
 } nn_serve_stats_t;
 
 void nn_serve_opts_default(nn_serve_opts *o);
 
 /* Starts a serving loop on the current device: a host scheduler thread
- * admits queued requests while resident device bytes stay within
- * hbm_budget_bytes and fewer than max_inflight run; each admitted request
- * is assembled and solved on its own stream, so solves of different
- * requests overlap on the device. */
+ * admits queued requests while the estimated device bytes of the admitted
+ * requests stay within hbm_budget_bytes, fewer than max_inflight run, and
+ * the request's thread blocks are sure to be co-resident with those of the
+ * running solves (each request's launch shape -- threads per block, blocks,
+ * whether a block takes a whole SM -- is fixed when it is submitted and
+ * charged against the SMs of the device; a request larger than about 32
+ * slices of 32 rows per SM takes the whole device).  Each admitted request
+ * is assembled and solved on its own stream, so solves of different requests
+ * overlap on the device. */
 nn_status nn_serve_create(size_t hbm_budget_bytes, const nn_serve_opts *o, nn_server **out);
 
-/* Queues a steady problem (host arrays, copied before return).  Returns
- * BUSY if the queue is full, INVALID_ARG/INFEASIBLE for invalid problems,
- * or INVALID_ARG if the problem alone exceeds the budget. */
-nn_status nn_serve_submit(nn_server *sv, const nn_problem *p, uint64_t *request_id);
+/* Queues a steady problem (host arrays, copied before return) with its own
+ * solver options o (NULL = the server's nn_serve_opts.solve; GPCG on the SELL
+ * format, NN_PREC_FP64 or NN_PREC_MIXED).  Returns BUSY if the queue is full,
+ * INVALID_ARG/INFEASIBLE for invalid problems or options, or INVALID_ARG if
+ * the problem alone exceeds the budget. */
+nn_status nn_serve_submit(nn_server *sv, const nn_problem *p, const nn_solve_opts *o, uint64_t *request_id);
 
 /* NN_OK and the solution in c_out [N] (host) once request id finished
  * (the request is then released); BUSY while queued or running; the

@@ -92,13 +92,14 @@ class nn_serve_stats_t(ctypes.Structure):
     _fields_ = [("submitted", c_int64), ("completed", c_int64), ("failed", c_int64), ("rejected", c_int64),
                 ("p50_ms", c_double), ("p99_ms", c_double), ("mean_ms", c_double), ("solves_per_s", c_double),
                 ("bytes_resident", c_size_t), ("bytes_peak", c_size_t), ("budget", c_size_t),
-                ("inflight_peak", c_int64)]
+                ("inflight_peak", c_int64), ("bytes_reserved_peak", c_size_t), ("estimate_overruns", c_int64),
+                ("estimate_max_ratio", c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
-EXPORTS = ["nn_last_error", "nn_version", "nn_kernel_launches", "nn_mesh_counts", "nn_mesh_structured", "nn_assemble_opts_default",
+EXPORTS = ["nn_last_error", "nn_version", "nn_kernel_launches", "nn_device_allocations", "nn_mesh_counts", "nn_mesh_structured", "nn_assemble_opts_default",
            "nn_assemble", "nn_system_destroy", "nn_system_describe", "nn_system_copy_out",
            "nn_solve_opts_default", "nn_qp_solve", "nn_step", "nn_transient", "nn_kkt_residual", "nn_spmv",
            "nn_spmv_mixed_noalloc",
@@ -124,6 +125,7 @@ def lib():
     L.nn_last_error.restype = ctypes.c_char_p
     L.nn_version.restype = ctypes.c_char_p
     L.nn_kernel_launches.restype = c_uint64
+    L.nn_device_allocations.restype = c_uint64
     L.nn_mesh_counts.argtypes = [c_int, c_int, c_int, c_int, POINTER(c_int64), POINTER(c_int64)]
     L.nn_mesh_structured.argtypes = [c_int, c_int, c_int, c_int, vp, vp, vp]
     L.nn_assemble_opts_default.argtypes = [POINTER(nn_assemble_opts)]
@@ -152,7 +154,7 @@ def lib():
     L.nn_serve_opts_default.argtypes = [POINTER(nn_serve_opts)]
     L.nn_serve_opts_default.restype = None
     L.nn_serve_create.argtypes = [c_size_t, POINTER(nn_serve_opts), POINTER(vp)]
-    L.nn_serve_submit.argtypes = [vp, POINTER(nn_problem), POINTER(c_uint64)]
+    L.nn_serve_submit.argtypes = [vp, POINTER(nn_problem), POINTER(nn_solve_opts), POINTER(c_uint64)]
     L.nn_serve_poll.argtypes = [vp, c_uint64, vp, POINTER(nn_solve_info)]
     L.nn_serve_drain.argtypes = [vp]
     L.nn_serve_stats.argtypes = [vp, POINTER(nn_serve_stats_t)]
@@ -284,6 +286,10 @@ def nn_kernel_launches():
 
 
 kernel_launches = nn_kernel_launches
+
+
+def nn_device_allocations():
+    return int(lib().nn_device_allocations())
 
 
 def nn_mesh_counts(dim, nx, ny, nz=0):
@@ -452,11 +458,13 @@ def nn_serve_create(budget_bytes, opts=None):
     return Server(h.value)
 
 
-def nn_serve_submit(server, problem):
+def nn_serve_submit(server, problem, opts=None):
+    """opts: this request's nn_solve_opts (None = the server's)."""
     if not isinstance(problem, Problem):
         problem = Problem(problem)
     rid = c_uint64()
-    st = lib().nn_serve_submit(server.handle, byref(problem.c), byref(rid))
+    st = lib().nn_serve_submit(server.handle, byref(problem.c), byref(opts) if opts is not None else None,
+                               byref(rid))
     _check(st)
     return rid.value
 

@@ -782,6 +782,9 @@ nn_status assemble_impl(const nn_problem *p, const nn_assemble_opts *o, cudaStre
     s->b0norm = std::sqrt(hn[1]);
     s->has_csr = true;  // the reduced CSR is always kept (small next to SELL; used by nn_spmv)
     s->has_full = true;
+    // nothing is freed before this point: the most device memory the
+    // assembly held at once is the system plus every temporary
+    s->assembly_peak_bytes = s->arena.bytes + T.a.bytes;
     CUF(cudaGetLastError());
     *out = s;
     return NN_OK;

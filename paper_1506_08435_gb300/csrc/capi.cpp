@@ -39,9 +39,12 @@ cudaMemPool_t device_pool() {
     return g_pools[dev];
 }
 
+static std::atomic<uint64_t> g_allocs{0};
+
 cudaError_t pool_alloc(void **p, size_t bytes, cudaStream_t st) {
     cudaMemPool_t pool = device_pool();
     if (!pool) return cudaErrorMemoryAllocation;
+    g_allocs.fetch_add(1, std::memory_order_relaxed);
     return cudaMallocFromPoolAsync(p, bytes, pool, st);
 }
 
@@ -112,6 +115,8 @@ const char *nn_last_error(void) { return g_err; }
 const char *nn_version(void) { return "nnqp 0.1 (sm_103a)"; }
 
 uint64_t nn_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+uint64_t nn_device_allocations(void) { return g_allocs.load(std::memory_order_relaxed); }
 
 nn_status nn_mesh_counts(int dim, int nx, int ny, int nz, int64_t *n_nodes, int64_t *n_elems) {
     if ((dim != 2 && dim != 3) || nx < 1 || ny < 1 || (dim == 3 && nz < 1) || !n_nodes || !n_elems) {
@@ -293,7 +298,7 @@ nn_status nn_kkt_residual(const nn_system *s, const double *c, const double *c_p
 
 nn_status nn_spmv(const nn_system *s, const double *x, double *y, int format, int precision, void *stream) {
     clear_error();
-    if (!s || !x || !y) {
+    if (!s || ((!x || !y) && s->NF > 0)) {
         set_error("nn_spmv: NULL argument");
         return NN_ERR_INVALID_ARG;
     }
@@ -302,7 +307,7 @@ nn_status nn_spmv(const nn_system *s, const double *x, double *y, int format, in
 
 nn_status nn_spmv_mixed_noalloc(const nn_system *s, const double *x, double *y, void *stream) {
     clear_error();
-    if (!s || !x || !y) {
+    if (!s || ((!x || !y) && s->NF > 0)) {
         set_error("nn_spmv_mixed_noalloc: NULL argument");
         return NN_ERR_INVALID_ARG;
     }

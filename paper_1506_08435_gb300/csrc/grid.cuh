@@ -44,6 +44,7 @@ struct GridArgs {
     float *v32[13];         // d g p q r z s w gw r32 l32 h32 m2
     GpcgCtl ctl;
     double rtol, den_fallback, b0norm, inner_rtol;
+    int64_t inner_cap;      // mixed: products allowed to one FP32 inner solve
     int max_ref;
     GridBarrier *bar;
     double *partials;
@@ -190,11 +191,11 @@ __global__ void __launch_bounds__(TPB, TPB >= 512 ? 1 : mode_min_blocks(MODE)) k
             if constexpr (FMT == 2)
                 status = mixed_solve<CGV, true>(T, R, a.A, A32loc, a.lo, a.hi, b, x, v, a.v32[9], a.v32[10],
                                                  a.v32[11], v64, a.rtol * den, a.inner_rtol, a.max_ref,
-                                                 a.ctl.max_spmv, inner_product_cap(a.n), a.ctl, a.ctl, ms);
+                                                 a.ctl.max_spmv, a.inner_cap, a.ctl, a.ctl, ms);
             else
                 status = mixed_solve<CGV, true>(T, R, a.A, a.A32, a.lo, a.hi, b, x, v, a.v32[9], a.v32[10],
                                                  a.v32[11], v64, a.rtol * den, a.inner_rtol, a.max_ref,
-                                                 a.ctl.max_spmv, inner_product_cap(a.n), a.ctl, a.ctl, ms);
+                                                 a.ctl.max_spmv, a.inner_cap, a.ctl, a.ctl, ms);
             if (status == ST_TIMEOUT) return;
             cnt[1] += ms.spmv64;
             cnt[2] += ms.spmv32;

@@ -112,6 +112,7 @@ struct nn_system {
     nnqp::SellMat<double> M64;      // transient: off-diagonals of M_FF (shares sptr/col)
     double *mdiag64 = nullptr;      // [NF]
     double *b0 = nullptr;           // [NF] F_F - K_FD c_D
+    size_t assembly_peak_bytes = 0; // device bytes held at the end of assembly (system + temporaries)
     double anorm_inf = 0;           // ||A||_inf
     double b0norm = 0;              // ||b0||_2
     bool has_csr = false, has_mixed = false, has_full = false;

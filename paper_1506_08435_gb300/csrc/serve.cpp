@@ -3,16 +3,23 @@
 // Requests are queued by nn_serve_submit (host arrays copied at once).  A
 // scheduler thread admits the oldest queued request when (a) a worker slot
 // is free, (b) its device-memory estimate fits in the HBM budget next to the
-// requests already resident, and (c) its thread blocks fit in the SM-block
-// budget next to those of the requests already running.  Each worker owns a
-// CUDA stream: it assembles the request's system, solves it in one launch
-// and copies the solution back, so the device work of different requests
-// overlaps.  Every request is solved by a persistent cooperative grid of at
-// most a fixed share of the device (fewer blocks for small requests).
-// Because the blocks of all running solves fit on the device together, no
-// solve ever waits for blocks that cannot become resident.  (One thread-block
-// cluster per request was measured too: on 8-16 SMs a request's FP64 passes
-// take 3-10x longer than on its grid share, and small requests gain nothing.)
+// requests already resident, and (c) its thread blocks are sure to be
+// co-resident with those of the requests already running (admission.h: the
+// launch shape of every request -- threads per block, blocks, and whether a
+// block takes a whole SM -- is fixed at submit time and enforced at launch).
+// Each worker owns a CUDA stream: it assembles the request's system, solves
+// it in one persistent cooperative launch and copies the solution back, so
+// the device work of different requests overlaps.  Large requests take the
+// whole co-resident grid and run alone; small ones run side by side.  (One
+// thread-block cluster per request was measured too: on 8-16 SMs a request's
+// FP64 passes take 3-10x longer than on its grid share, and small requests
+// gain nothing.)
+//
+// Memory: admission charges each request an upper estimate of its device
+// bytes (estimate_bytes); the worker then measures what the request really
+// holds (the assembled system, the assembly's temporaries, the solve's
+// scratch and the solution vector) and the statistics report those measured
+// bytes, plus every request whose measured bytes exceeded its estimate.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -27,14 +34,15 @@
 #include <thread>
 #include <vector>
 #include "internal.h"
+#include "admission.h"
 
 namespace nnqp {
 
 nn_status assemble_impl(const nn_problem *p, const nn_assemble_opts *o, cudaStream_t st, nn_system **out);
 nn_status check_opts(const nn_solve_opts *o);
 nn_status serve_solve(nn_system *s, const nn_solve_opts *o, const double *c_in_dev, double *c_out_dev,
-                      cudaStream_t st, int grid_blocks, nn_solve_info *info);
-int solve_grid_capacity();
+                      cudaStream_t st, int tpb, int grid_blocks, nn_solve_info *info, size_t *plan_bytes);
+int solve_grid_blocks_per_sm(int *sms);
 
 using Clock = std::chrono::steady_clock;
 
@@ -45,9 +53,11 @@ struct Request {
     std::vector<int32_t> conn;
     std::vector<uint8_t> dmask;
     int64_t N = 0, E = 0;
-    size_t bytes = 0;
-    int blocks = 0;
-    Clock::time_point t_submit, t_done;
+    nn_solve_opts opts{};         // this request's solver options
+    size_t bytes = 0;             // admission estimate
+    size_t measured = 0;          // device bytes the request really held
+    RequestShape shape;
+    Clock::time_point t_submit, t_start, t_done;   // t_start: a worker took it (device work begins)
     std::vector<double> result;
     nn_solve_info info{};
     nn_status status = NN_ERR_BUSY;
@@ -59,15 +69,18 @@ struct Server {
     size_t budget = 0;
     nn_serve_opts opts{};
     int device = 0;
-    int capacity = 0;             // co-resident blocks of the solve kernel on the device
+    BlockLedger ledger;           // blocks of the running solves, by class
     std::mutex mu;
     std::condition_variable cv_sched, cv_done;
     std::deque<std::shared_ptr<Request>> queue;
     std::map<uint64_t, std::shared_ptr<Request>> table;
     std::deque<std::shared_ptr<Request>> ready;      // admitted, waiting for a worker
     uint64_t next_id = 1;
-    size_t resident = 0, peak = 0;
-    int blocks_in_use = 0;
+    size_t reserved = 0, reserved_peak = 0;   // admission estimates of the running requests
+    struct Held { Clock::time_point t0, t1; size_t bytes; };
+    std::vector<Held> held;                   // measured device bytes of every finished request
+    int64_t overruns = 0;                     // requests whose measured bytes exceeded the estimate
+    double worst_ratio = 0.0;                 // largest measured / estimate
     int inflight = 0;
     int64_t inflight_peak = 0;
     int64_t submitted = 0, completed = 0, failed = 0, rejected = 0;
@@ -81,10 +94,14 @@ struct Server {
 
 namespace {
 
-// Upper estimate of the device bytes one request holds while it runs.
-size_t estimate_bytes(int dim, int64_t N, int64_t E) {
+// Upper estimate of the device bytes one request holds while it runs (the
+// most of: assembly with its temporaries -- element matrices, incidence
+// lists, scans -- or the assembled system with the solve's vectors); the
+// mixed path adds its FP32 operator values and vectors.  Checked against the
+// measured bytes of every served request (estimate_overruns).
+size_t estimate_bytes(int dim, int64_t N, int64_t E, bool mixed) {
     const double nnz = (dim == 3 ? 16.0 : 7.5) * (double)N;
-    const double b = 52.0 * nnz + 300.0 * N + (dim == 3 ? 150.0 : 110.0) * E + (4 << 20);
+    const double b = 52.0 * nnz + (mixed ? 360.0 : 300.0) * N + (dim == 3 ? 150.0 : 110.0) * E + (4 << 20);
     return (size_t)b;
 }
 
@@ -100,19 +117,24 @@ void worker_loop(Server *sv) {
             if (sv->stop && sv->ready.empty()) break;
             r = sv->ready.front();
             sv->ready.pop_front();
+            r->t_start = Clock::now();
         }
         nn_assemble_opts ao;
         nn_assemble_opts_default(&ao);
-        ao.build_mixed = sv->opts.solve.precision == NN_PREC_MIXED;
+        ao.build_mixed = r->opts.precision == NN_PREC_MIXED;
         nn_system *s = nullptr;
         nn_status stt = assemble_impl(&r->p, &ao, st, &s);
         double *dc = nullptr;
+        size_t plan_bytes = 0, measured = 0;
         if (stt == NN_OK) {
             if (pool_alloc((void **)&dc, sizeof(double) * r->N, st) != cudaSuccess) stt = NN_ERR_OOM;
         }
         if (stt == NN_OK) {
             cudaMemsetAsync(dc, 0, sizeof(double) * r->N, st);
-            stt = serve_solve(s, &sv->opts.solve, dc, dc, st, r->blocks, &r->info);
+            stt = serve_solve(s, &r->opts, dc, dc, st, r->shape.tpb, r->shape.blocks, &r->info, &plan_bytes);
+            // the most the request held at once: the assembly's peak (system +
+            // temporaries), or the system + solution vector + solve scratch
+            measured = std::max(s->assembly_peak_bytes, s->arena.bytes + sizeof(double) * r->N + plan_bytes);
             if (stt == NN_OK || stt == NN_ERR_NOT_CONVERGED) {
                 r->result.resize(r->N);
                 cudaError_t e = cudaMemcpyAsync(r->result.data(), dc, sizeof(double) * r->N,
@@ -137,8 +159,12 @@ void worker_loop(Server *sv) {
             if (stt != NN_OK && stt != NN_ERR_NOT_CONVERGED) r->error = nn_last_error();
             r->t_done = Clock::now();
             r->done = true;
-            sv->resident -= r->bytes;
-            sv->blocks_in_use -= r->blocks;
+            r->measured = measured;
+            if (measured > r->bytes) ++sv->overruns;
+            sv->worst_ratio = std::max(sv->worst_ratio, (double)measured / (double)r->bytes);
+            if (measured > 0) sv->held.push_back({r->t_start, r->t_done, measured});
+            sv->reserved -= r->bytes;
+            sv->ledger.release(r->shape);
             --sv->inflight;
             if (stt == NN_OK) {
                 ++sv->completed;
@@ -163,15 +189,15 @@ void sched_loop(Server *sv) {
             if (sv->stop) return true;
             if (sv->queue.empty()) return false;
             const auto &r = sv->queue.front();
-            return sv->inflight < sv->opts.max_inflight && sv->resident + r->bytes <= sv->budget &&
-                   sv->blocks_in_use + r->blocks <= sv->capacity;
+            return sv->inflight < sv->opts.max_inflight && sv->reserved + r->bytes <= sv->budget &&
+                   sv->ledger.can_admit(r->shape);
         });
         if (sv->stop) break;
         auto r = sv->queue.front();
         sv->queue.pop_front();
-        sv->resident += r->bytes;
-        sv->peak = std::max(sv->peak, sv->resident);
-        sv->blocks_in_use += r->blocks;
+        sv->reserved += r->bytes;
+        sv->reserved_peak = std::max(sv->reserved_peak, sv->reserved);
+        sv->ledger.admit(r->shape);
         ++sv->inflight;
         sv->inflight_peak = std::max<int64_t>(sv->inflight_peak, sv->inflight);
         sv->ready.push_back(r);
@@ -218,8 +244,11 @@ nn_status nn_serve_create(size_t hbm_budget_bytes, const nn_serve_opts *o, nn_se
     sv->budget = hbm_budget_bytes;
     sv->opts = *o;
     cudaGetDevice(&sv->device);
-    sv->capacity = solve_grid_capacity();
-    if (sv->capacity < 1) {
+    int sms = 0;
+    const int per = solve_grid_blocks_per_sm(&sms);
+    sv->ledger.sms = sms;
+    sv->ledger.small_per_sm = per;
+    if (per < 1 || sms < 1 || per > 64) {
         delete h;
         set_error("nn_serve_create: cannot size the solve kernel on this device");
         return NN_ERR_CUDA;
@@ -230,7 +259,7 @@ nn_status nn_serve_create(size_t hbm_budget_bytes, const nn_serve_opts *o, nn_se
     return NN_OK;
 }
 
-nn_status nn_serve_submit(nn_server *h, const nn_problem *p, uint64_t *request_id) {
+nn_status nn_serve_submit(nn_server *h, const nn_problem *p, const nn_solve_opts *o, uint64_t *request_id) {
     clear_error();
     if (!h || !p || !request_id) {
         set_error("nn_serve_submit: NULL argument");
@@ -253,7 +282,14 @@ nn_status nn_serve_submit(nn_server *h, const nn_problem *p, uint64_t *request_i
         set_error("nn_serve_submit: serving takes steady problems");
         return NN_ERR_INVALID_ARG;
     }
+    if (!o) o = &sv->opts.solve;
+    NN_TRY(check_opts(o));
+    if (o->solver != NN_SOLVER_GPCG || o->format != NN_FMT_SELL) {
+        set_error("nn_serve_submit: served requests are solved by GPCG on the SELL format");
+        return NN_ERR_INVALID_ARG;
+    }
     auto r = std::make_shared<Request>();
+    r->opts = *o;
     const int dim = p->dim, nv = dim + 1;
     if (p->coords) {
         r->N = p->n_nodes;
@@ -265,19 +301,21 @@ nn_status nn_serve_submit(nn_server *h, const nn_problem *p, uint64_t *request_i
         set_error("nn_serve_submit: empty mesh");
         return NN_ERR_INVALID_ARG;
     }
-    r->bytes = estimate_bytes(dim, r->N, r->E);
+    r->bytes = estimate_bytes(dim, r->N, r->E, r->opts.precision == NN_PREC_MIXED);
     if (r->bytes > sv->budget) {
         set_error("nn_serve_submit: the request alone (%zu bytes) exceeds the budget", r->bytes);
         return NN_ERR_INVALID_ARG;
     }
-    // persistent grid: one block per 8 slices, at most the share.  By default
-    // the share is the whole co-resident grid: a large request then runs
-    // alone at full speed (bandwidth- and FP64-bound solves gain nothing from
-    // sharing the device, and co-resident blocks of other grids slow their
-    // barriers), while small requests, whose grids are small, run side by side.
-    const int64_t slices = (r->N + 31) / 32;
-    const int share = sv->opts.sm_share_blocks > 0 ? sv->opts.sm_share_blocks : sv->capacity;
-    r->blocks = (int)std::max<int64_t>(1, std::min<int64_t>((slices + 7) / 8, std::min(share, sv->capacity)));
+    // launch shape, fixed now (the free unknowns are at most the nodes):
+    // large requests take the whole co-resident grid and run alone at full
+    // speed (bandwidth- and FP64-bound solves gain nothing from sharing the
+    // device, and blocks of other grids slow their barriers), small ones run
+    // side by side
+    r->shape = request_shape((r->N + 31) / 32, sv->ledger.sms, sv->ledger.small_per_sm, sv->opts.sm_share_blocks);
+    if (!sv->ledger.fits_alone(r->shape)) {
+        set_error("nn_serve_submit: the request's grid does not fit on the device");
+        return NN_ERR_INVALID_ARG;
+    }
     const int ncoef = p->coef_kind == NN_COEF_TENSOR ? (dim == 2 ? 3 : 6) : dim;
     r->coef.assign(p->coef, p->coef + (size_t)r->E * ncoef);
     if (p->f_elem) r->fel.assign(p->f_elem, p->f_elem + r->E);
@@ -362,10 +400,31 @@ nn_status nn_serve_stats(nn_server *h, nn_serve_stats_t *st) {
     st->completed = sv->completed;
     st->failed = sv->failed;
     st->rejected = sv->rejected;
-    st->bytes_resident = sv->resident;
-    st->bytes_peak = sv->peak;
+    st->bytes_resident = sv->reserved;
+    // largest sum of measured bytes over requests that held device memory at
+    // the same time (a sweep over their [start, done] intervals)
+    {
+        std::vector<std::pair<Clock::time_point, int64_t>> ev;
+        ev.reserve(sv->held.size() * 2);
+        for (const auto &h : sv->held) {
+            ev.push_back({h.t0, (int64_t)h.bytes});
+            ev.push_back({h.t1, -(int64_t)h.bytes});
+        }
+        std::sort(ev.begin(), ev.end(), [](const auto &a, const auto &b) {
+            return a.first < b.first || (a.first == b.first && a.second < b.second);
+        });
+        int64_t cur = 0, best = 0;
+        for (const auto &e : ev) {
+            cur += e.second;
+            best = std::max(best, cur);
+        }
+        st->bytes_peak = (size_t)best;
+    }
     st->budget = sv->budget;
     st->inflight_peak = sv->inflight_peak;
+    st->bytes_reserved_peak = sv->reserved_peak;
+    st->estimate_overruns = sv->overruns;
+    st->estimate_max_ratio = sv->worst_ratio;
     if (!sv->lat_ms.empty()) {
         std::vector<double> v = sv->lat_ms;
         std::sort(v.begin(), v.end());

@@ -281,8 +281,11 @@ struct GridPlan {
     DevArena arena;
 };
 
-// Builds plan P (its scratch is allocated on stream st).
-nn_status plan_build(nn_system *s, const nn_solve_opts *o, int mode, int nsteps, cudaStream_t st, GridPlan &P) {
+// Builds plan P (its scratch is allocated on stream st).  force_tpb = 256 or
+// 512 fixes the threads per block (serving decides the launch shape before
+// admission); 0 lets the size decide.
+nn_status plan_build(nn_system *s, const nn_solve_opts *o, int mode, int nsteps, cudaStream_t st, GridPlan &P,
+                     int force_tpb = 0) {
     const int64_t n = s->NF, N = s->N;
     const bool mixed = mode_mixed(mode);
     const int fmt = o->format;
@@ -344,7 +347,13 @@ nn_status plan_build(nn_system *s, const nn_solve_opts *o, int mode, int nsteps,
     // passes stream HBM and the pipelined form's extra vector streams cost
     // more than its saved barriers (measured: 40^3 transient 71.6 -> 64.4 ms,
     // 50^2 steady 4.5 -> 4.0 ms; 150^3 steady 4.12 -> 4.31 s)
-    a.ctl.cg_variant = n < (1 << 20) ? 2 : 0;
+    // NNQP_FORCE_LARGE=1 runs a system of any size the way the largest ones
+    // run (streamed operator, textbook CG, the full co-resident grid of
+    // 256-thread blocks): it lets the tests check that path against the
+    // oracle at sizes the oracle solves in seconds
+    const char *fl = getenv("NNQP_FORCE_LARGE");
+    const bool force_large = o->solver == NN_SOLVER_GPCG && fl && fl[0] == '1';
+    a.ctl.cg_variant = n < (1 << 20) && !force_large ? 2 : 0;
     if (fmt == NN_FMT_CSR && a.ctl.cg_variant == 2) a.ctl.cg_variant = 1;   // CSR kernels: forms 0 and 1
     a.ctl.cg_bound_stop = 0;
     if (const char *e = getenv("NNQP_CG_VARIANT")) a.ctl.cg_variant = atoi(e);
@@ -356,6 +365,8 @@ nn_status plan_build(nn_system *s, const nn_solve_opts *o, int mode, int nsteps,
     a.den_fallback = den_fallback(s);
     a.b0norm = s->b0norm;
     a.inner_rtol = o->inner_rtol;
+    a.inner_cap = inner_product_cap(n);
+    if (const char *e = getenv("NNQP_INNER_CAP")) a.inner_cap = std::max<int64_t>(1, atoll(e));
     a.max_ref = 200;
     a.timeout_ns = (unsigned long long)(o->wait_timeout_s * 1e9);
     // grid
@@ -386,6 +397,12 @@ nn_status plan_build(nn_system *s, const nn_solve_opts *o, int mode, int nsteps,
     const bool driver = lbfgs || tron;   // solvers with a kernel of their own
     if (!driver && slices <= (int64_t)4 * 8 * sms && slices > (int64_t)8 * sms / 2) tpb = 512;
     if (const char *e = getenv("NNQP_GRID_THREADS")) tpb = atoi(e);
+    if (!driver && (force_tpb == 256 || force_tpb == 512)) tpb = force_tpb;
+    if (force_large) {
+        tpb = kSolveThreads;
+        a.A.stream = true;
+        a.A32.stream = true;
+    }
     GridKernel kern = lbfgs ? k_lbfgs_grid : tron ? k_tron_grid : grid_kernel(mode, fmt, a.ctl.cg_variant, tpb);
     if (!kern && !driver && tpb != kSolveThreads) {
         tpb = kSolveThreads;
@@ -408,6 +425,7 @@ nn_status plan_build(nn_system *s, const nn_solve_opts *o, int mode, int nsteps,
     const int64_t spread = std::max<int64_t>(by_rows, (slices + 3) / 4);
     int want = (int)std::min<int64_t>(spread, slices <= (int64_t)4 * 8 * sms ? (int64_t)sms : (int64_t)maxg);
     want = std::min(want, maxg);
+    if (force_large) want = maxg;
     if (o->grid_blocks > 0) want = std::min(o->grid_blocks, maxg);
     want = std::max(want, 1);
     // Mid-size SELL solves keep each block's slices of the operator of the
@@ -517,15 +535,19 @@ nn_status plan_collect(GridPlan &P, cudaStream_t st, float ms, nn_solve_info *in
 
 // Runs the persistent solve kernel once: plan, launch, records, release.
 // c_in/c_out/c_hist are device arrays.
+// force_tpb: as for plan_build; plan_bytes (optional) receives the plan's
+// scratch bytes.
 nn_status run_grid(nn_system *s, const nn_solve_opts *o, int mode, int nsteps, const double *c_in, double *c_out,
-                   double *c_hist, cudaStream_t st, nn_solve_info *infos, int ninfos) {
+                   double *c_hist, cudaStream_t st, nn_solve_info *infos, int ninfos, int force_tpb = 0,
+                   size_t *plan_bytes = nullptr) {
     GridPlan P;
     struct Release {
         GridPlan &p;
         cudaStream_t st;
         ~Release() { p.arena.release(st); }
     } rel{P, st};
-    NN_TRY(plan_build(s, o, mode, nsteps, st, P));
+    NN_TRY(plan_build(s, o, mode, nsteps, st, P, force_tpb));
+    if (plan_bytes) *plan_bytes = P.arena.bytes;
     cudaEvent_t e0, e1;
     NN_CUDA_TRY(cudaEventCreate(&e0));
     NN_CUDA_TRY(cudaEventCreate(&e1));
@@ -592,11 +614,22 @@ nn_status kkt_impl(const nn_system *s, const double *c, const double *c_prev, in
 
 nn_status spmv_impl(const nn_system *s, const double *x, double *y, int format, int precision, cudaStream_t st) {
     const int nb = (int)std::max<int64_t>((s->A64.nslices + 7) / 8, 1);
+    if ((format != NN_FMT_SELL && format != NN_FMT_CSR) || (precision != NN_PREC_FP64 && precision != NN_PREC_MIXED)) {
+        set_error("nn_spmv: format must be NN_FMT_SELL or NN_FMT_CSR, precision NN_PREC_FP64 or NN_PREC_MIXED");
+        return NN_ERR_INVALID_ARG;
+    }
+    if (precision == NN_PREC_MIXED && format != NN_FMT_SELL) {
+        set_error("nn_spmv: the FP32-value operator is stored in SELL format only");
+        return NN_ERR_INVALID_ARG;
+    }
+    if (precision == NN_PREC_MIXED && !s->has_mixed) {
+        set_error("nn_spmv: system has no FP32 copy (build_mixed = 0)");
+        return NN_ERR_INVALID_ARG;
+    }
+    // nn_assemble refuses systems without free unknowns; a zero-size grid
+    // would be a launch error, so an empty product returns before any launch
+    if (s->NF == 0) return NN_OK;
     if (precision == NN_PREC_MIXED) {
-        if (!s->has_mixed) {
-            set_error("nn_spmv: system has no FP32 copy (build_mixed = 0)");
-            return NN_ERR_INVALID_ARG;
-        }
         Scratch S;
         S.st = st;
         float *x32;
@@ -664,6 +697,7 @@ nn_status spmv_mixed_noalloc_impl(const nn_system *s, const double *x, double *y
                   (long long)s->NF, (long long)kNoAllocMaxFree);
         return NN_ERR_INVALID_ARG;
     }
+    if (s->NF == 0) return NN_OK;   // as in spmv_impl: no launch for an empty product
     float *x32 = nullptr;
     NN_TRY(noalloc_scratch(&x32));
     const int nb = (int)std::max<int64_t>((s->A64.nslices + 7) / 8, 1);
@@ -700,21 +734,27 @@ int mode_for(const nn_system *s, const nn_solve_opts *o) {
     return o->precision == NN_PREC_MIXED ? MODE_MIXED : MODE_STEADY;
 }
 
-// Co-resident blocks of the steady/mixed solve kernel on the current device.
-int solve_grid_capacity() {
+// Co-resident 256-thread blocks per SM of the steady/mixed solve kernels
+// (the smallest over modes and CG forms) and the SM count of the current
+// device.
+int solve_grid_blocks_per_sm(int *sms) {
     int c = 1 << 30;
     for (int mode : {MODE_STEADY, MODE_MIXED})
         for (int v = 0; v < 3; ++v)
-            if (GridKernel k = grid_kernel(mode, NN_FMT_SELL, v)) c = std::min(c, max_coresident(k));
+            if (GridKernel k = grid_kernel(mode, NN_FMT_SELL, v)) c = std::min(c, max_coresident(k) / device_sms());
+    if (sms) *sms = device_sms();
     return c;
 }
 
-// One steady solve with a fixed persistent grid (serving).
+// One steady solve with the launch shape fixed at admission (serving):
+// tpb threads per block, at most grid_blocks blocks.  plan_bytes receives
+// the solve's scratch bytes.
 nn_status serve_solve(nn_system *s, const nn_solve_opts *o, const double *c_in_dev, double *c_out_dev,
-                      cudaStream_t st, int grid_blocks, nn_solve_info *info) {
+                      cudaStream_t st, int tpb, int grid_blocks, nn_solve_info *info, size_t *plan_bytes) {
     nn_solve_opts q = *o;
     q.grid_blocks = grid_blocks;
-    return run_grid(s, &q, mode_for(s, &q), 1, c_in_dev, c_out_dev, nullptr, st, info, info ? 1 : 0);
+    return run_grid(s, &q, mode_for(s, &q), 1, c_in_dev, c_out_dev, nullptr, st, info, info ? 1 : 0, tpb,
+                    plan_bytes);
 }
 
 }  // namespace nnqp

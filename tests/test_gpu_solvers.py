@@ -1,6 +1,7 @@
 """Parity of the projected L-BFGS solver, the batched persistent solve and
 the serving loop with the FP64 oracle; alone-vs-in-the-mix equality."""
 import math
+import os
 import time
 
 import numpy as np
@@ -297,7 +298,10 @@ def test_serving_budget_admission_and_rejection():
     P.nn_serve_drain(sv)
     st = P.nn_serve_stats(sv)
     assert st["completed"] == len(specs)
-    assert st["bytes_peak"] <= st["budget"]
+    assert st["bytes_reserved_peak"] <= st["budget"]
+    # measured bytes: never above the estimates admission charged
+    assert st["estimate_overruns"] == 0 and 0.0 < st["estimate_max_ratio"] <= 1.0, st
+    assert st["bytes_peak"] <= st["bytes_reserved_peak"] <= st["budget"]
     for rid, sp in zip(ids, specs):
         assert P.nn_serve_poll(sv, rid, np.zeros(sp.n_nodes))["status"] == 0
     # a request larger than the whole budget is refused at submit
@@ -374,3 +378,69 @@ def test_plan_rejects_bad_arguments():
     with pytest.raises(P.NnError):
         plan.launch(None, None)
     plan.close()
+
+
+def test_serving_mid_size_requests_are_not_co_scheduled_beyond_the_sms():
+    """Requests of ~36k nodes get one 512-thread block per SM on 128 SMs:
+    two of them do not fit the 152 SMs together, so admission runs them one
+    after the other (each grid must be wholly resident to pass its barriers),
+    while small requests still run beside each other."""
+    mids = [I.config3_steady_3d(n=32, seed=s) for s in (11, 12, 13)]
+    sv = P.nn_serve_create(16 << 30, P.serve_opts(max_inflight=4))
+    ids = [P.nn_serve_submit(sv, P.Problem(sp)) for sp in mids]
+    P.nn_serve_drain(sv)
+    st = P.nn_serve_stats(sv)
+    outs = []
+    for rid, sp in zip(ids, mids):
+        c = np.zeros(sp.n_nodes)
+        assert P.nn_serve_poll(sv, rid, c)["status"] == 0
+        outs.append(c)
+    P.nn_serve_destroy(sv)
+    assert st["completed"] == 3 and st["failed"] == 0
+    assert st["inflight_peak"] == 1, st
+    red, b, x_ref, _ = oracle_solution(mids[0], threads=os.cpu_count() or 1)
+    compare_solution(outs[0][red.free], x_ref, red.A, b, mids[0].lo, mids[0].hi)
+    smalls = [sp for sp in _serve_specs(8) if sp.n_nodes < 15000][:4]
+    sv = P.nn_serve_create(16 << 30, P.serve_opts(max_inflight=4))
+    ids = [P.nn_serve_submit(sv, P.Problem(sp)) for sp in smalls]
+    P.nn_serve_drain(sv)
+    st = P.nn_serve_stats(sv)
+    P.nn_serve_destroy(sv)
+    assert st["completed"] == len(smalls) and st["inflight_peak"] > 1, st
+
+
+def test_serving_per_request_options_and_measured_bytes_within_the_estimate():
+    """Each request carries its own solver options (FP64 or mixed precision,
+    tolerance); every result meets the oracle's KKT test, mixed requests
+    refine in FP64, and the device bytes each request really held (assembly
+    with temporaries, or system + solution + scratch) stay within the
+    estimate admission charged for it, over 2D and 3D requests up to ~0.5M
+    nodes."""
+    specs = [I.serve_request(r) for r in range(40)]
+    specs = sorted([sp for sp in specs if sp.n_nodes <= 500_000], key=lambda sp: sp.n_nodes)
+    pick = specs[::max(1, len(specs) // 8)][:8] + [specs[-1]]
+    sv = P.nn_serve_create(32 << 30, P.serve_opts(max_inflight=4))
+    opts = [P.solve_opts(precision=P.NN_PREC_MIXED if k % 2 else P.NN_PREC_FP64, rtol=1e-10) for k in range(len(pick))]
+    ids = [P.nn_serve_submit(sv, P.Problem(sp), o) for sp, o in zip(pick, opts)]
+    P.nn_serve_drain(sv)
+    infos, outs = [], []
+    for rid, sp in zip(ids, pick):
+        c = np.zeros(sp.n_nodes)
+        infos.append(P.nn_serve_poll(sv, rid, c))
+        outs.append(c)
+    st = P.nn_serve_stats(sv)
+    P.nn_serve_destroy(sv)
+    assert st["completed"] == len(pick) and st["failed"] == 0
+    assert st["estimate_overruns"] == 0 and 0.0 < st["estimate_max_ratio"] <= 1.0, st
+    for k, (sp, c, info) in enumerate(zip(pick, outs, infos)):
+        assert info["status"] == 0
+        assert (info["refinements"] > 0) == (k % 2 == 1), (k, info)
+        _, red = oracle_reduced(sp)
+        kk = O.kkt(red.A, red.rhs(), sp.lo, sp.hi, c[red.free])
+        assert kk["bounds_ok"] and kk["kkt_rel"] <= 1e-8, (k, kk)
+    # options are checked at submit
+    sv = P.nn_serve_create(1 << 30)
+    with pytest.raises(P.NnError) as e:
+        P.nn_serve_submit(sv, P.Problem(pick[0]), P.solve_opts(solver=P.NN_SOLVER_LBFGS))
+    assert e.value.status == P.NN_ERR_INVALID_ARG
+    P.nn_serve_destroy(sv)

@@ -117,15 +117,28 @@ def test_reference_arm_prints_the_contract_line():
     """bench.py --impl reference times the oracle (CPU, no GPU needed) on the
     default workload and prints one JSON line with the contract's keys and
     the same config as the GPU arm."""
-    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
-                          "--warmup", "0"], capture_output=True, text=True, timeout=600,
-                         env=dict(os.environ, CUDA_VISIBLE_DEVICES=""))
-    assert out.returncode == 0, out.stderr[-800:]
     import json
-    line = json.loads(out.stdout.strip().splitlines()[-1])
+    sys.path.insert(0, ROOT)
+    import bench
+
+    def run(*extra):
+        out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                              "--warmup", "0", *extra], capture_output=True, text=True, timeout=600,
+                             env=dict(os.environ, CUDA_VISIBLE_DEVICES=""))
+        assert out.returncode == 0, out.stderr[-800:]
+        return json.loads(out.stdout.strip().splitlines()[-1])
+
+    # the default workload's family (steady 3D, rotated dispersion), shrunk
+    # to 40^3 so that the oracle's own assembly fits a CPU test
+    line = run("--workload", "steady3d", "--n", "40")
     assert line["impl"] == "reference" and line["metric"] == "QP solves/s" and line["value"] > 0
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
+    assert "MPRGP" in line["cpu_baseline"]["sample"]
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
+    assert line["config"]["workload"] == "steady3d_n40" and line["config"]["free"] == 66799
+    args = bench.argparse.Namespace(n=40, rtol=1e-10, solver="gpcg", ksp_rtol=0.1, precision="both")
+    assert line["config"] == bench.steady3d_config(I.config3_steady_3d(n=40), 40, args)
+    line = run("--workload", "transient3d")
     assert line["config"]["workload"] == "transient3d_n40_dt0.01_50steps"
     assert line["config"]["mass"] == "consistent" and line["config"]["solver"] == "gpcg"
 

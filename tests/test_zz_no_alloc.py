@@ -6,8 +6,9 @@ application whose device memory belongs entirely to another allocator).
 nn_spmv_mixed_noalloc serves them: it computes the FP32-value product of
 nn_spmv(NN_PREC_MIXED) with the library's fixed scratch array instead of a
 per-call temporary.  These tests call it through the C ABI and compare it
-with the allocating entry point on two calls in a row, and check that a
-system above the array's limit is refused.  This file is collected last.
+with the allocating entry point on two calls in a row, check that repeated
+calls take no device memory, and that a system above the array's limit is
+refused.  This file is collected last.
 """
 import numpy as np
 import pytest
@@ -57,6 +58,37 @@ def test_noalloc_product_matches_allocating_product_twice(dev, spec_fn):
         scale = np.add.reduceat(aval * xa[col], rp[:-1])
         assert np.all(np.isfinite(yn))
         assert np.all(np.abs(yn - yr) <= 2e-6 * scale)
+
+
+def test_noalloc_product_allocates_nothing_on_repeated_calls(dev):
+    """After the first call (which may load the library's module and look up
+    the array's address), further calls take no buffer from the library's
+    memory pool and leave the device's free memory unchanged; each still
+    gives the allocating product's result."""
+    spec = I.config3_steady_3d(n=20, seed=7)
+    s = P.nn_assemble(P.Problem(spec, device=dev), P.assemble_opts(build_mixed=1))
+    nf = s.describe()["n_free"]
+    rng = np.random.default_rng(3)
+    x = torch.tensor(rng.uniform(-1.0, 1.0, nf), device=dev)
+    y = torch.empty_like(x)
+    y_ref = torch.empty_like(x)
+    P.nn_spmv(s, x, y_ref, P.NN_FMT_SELL, P.NN_PREC_MIXED)
+    P.nn_spmv_mixed_noalloc(s, x, y)            # first call: set-up
+    torch.cuda.synchronize()
+    a0 = P.nn_device_allocations()
+    free0 = torch.cuda.mem_get_info()[0]
+    l0 = P.nn_kernel_launches()
+    for _ in range(50):
+        P.nn_spmv_mixed_noalloc(s, x, y)
+    torch.cuda.synchronize()
+    assert P.nn_device_allocations() == a0
+    assert torch.cuda.mem_get_info()[0] == free0
+    assert P.nn_kernel_launches() - l0 == 100   # two kernels per call, nothing else
+    assert torch.equal(y, y_ref)                 # same kernels, same FP32 arithmetic
+    # the allocating entry point does take a buffer per call (the counter sees it)
+    P.nn_spmv(s, x, y_ref, P.NN_FMT_SELL, P.NN_PREC_MIXED)
+    torch.cuda.synchronize()
+    assert P.nn_device_allocations() == a0 + 1
 
 
 def test_noalloc_product_rejects_systems_above_the_limit(dev):

@@ -65,11 +65,41 @@ __device__ __forceinline__ V proj_grad(V x, V g, V l, V h) {
     return g;
 }
 
+// Per-thread partial sum of a dot product over the thread's rows.  FP64
+// terms add plainly.  FP32 terms (the mixed-precision inner solves) add with
+// Kahan's compensation, so a thread's partial keeps close to FP64 accuracy
+// however many rows it sums, for three more FP32 operations per term (the
+// FP32 pipe is wide; GB300's FP64 pipe is not).  The partial enters the FP64
+// team reduction as sum - compensation, rounded once to FP64.
+template <typename V>
+struct Acc {
+    V s = (V)0;
+    __device__ __forceinline__ void operator+=(V x) { s += x; }
+    __device__ __forceinline__ double value() const { return (double)s; }
+};
+template <>
+struct Acc<float> {
+    float s = 0.0f, c = 0.0f;
+    __device__ __forceinline__ void operator+=(float x) {
+        const float y = x - c;
+        const float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+
 // Team reduction of per-thread partials kept in V.
 template <class Team, typename V, int K>
 __device__ __forceinline__ bool team_sum(Team &T, const V (&acc)[K], double (&out)[K]) {
 #pragma unroll
     for (int k = 0; k < K; ++k) out[k] = (double)acc[k];
+    return T.reduce(out);
+}
+template <class Team, typename V, int K>
+__device__ __forceinline__ bool team_sum(Team &T, const Acc<V> (&acc)[K], double (&out)[K]) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) out[k] = acc[k].value();
     return T.reduce(out);
 }
 
@@ -79,11 +109,8 @@ __device__ __forceinline__ bool team_sum(Team &T, const V (&acc)[K], double (&ou
 // instruction occupies the SM's narrow FP64 pipe for many cycles, so a
 // scalar division repeated by all warps of a block costs as much as the
 // reduction itself.
-template <class Team, typename V, int K, int M, class F>
-__device__ __forceinline__ bool team_sum_scalar(Team &T, const V (&acc)[K], double (&d)[K], double (&out)[M],
-                                                F &&f) {
-#pragma unroll
-    for (int k = 0; k < K; ++k) d[k] = (double)acc[k];
+template <class Team, int K, int M, class F>
+__device__ __forceinline__ bool team_sum_scalar_d(Team &T, double (&d)[K], double (&out)[M], F &&f) {
     if (!T.reduce(d)) return false;
     RedSmem &sm = *T.sm;
     if ((threadIdx.x >> 5) == 0) {
@@ -96,8 +123,23 @@ __device__ __forceinline__ bool team_sum_scalar(Team &T, const V (&acc)[K], doub
     __syncthreads();
 #pragma unroll
     for (int j = 0; j < M; ++j) out[j] = sm.sc[j];
-    __syncthreads();
+    // the next writer of sc is warp 0 after the next reduction, which
+    // begins with a block barrier
     return true;
+}
+template <class Team, typename V, int K, int M, class F>
+__device__ __forceinline__ bool team_sum_scalar(Team &T, const Acc<V> (&acc)[K], double (&d)[K], double (&out)[M],
+                                                F &&f) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) d[k] = acc[k].value();
+    return team_sum_scalar_d(T, d, out, f);
+}
+template <class Team, typename V, int K, int M, class F>
+__device__ __forceinline__ bool team_sum_scalar(Team &T, const V (&acc)[K], double (&d)[K], double (&out)[M],
+                                                F &&f) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) d[k] = (double)acc[k];
+    return team_sum_scalar_d(T, d, out, f);
 }
 
 __device__ __forceinline__ bool flag_set(double f) { return __double_as_longlong(f) != 0; }
@@ -205,7 +247,7 @@ __device__ int gpcg_solve(Team &T, const Rows &R, const Op &A, const Bounds<V> &
     st.vec += 2;
     if (!T.sync()) return ST_TIMEOUT;
     {
-        V a[1] = {zero};
+        Acc<V> a[1];
         double d[1];
         A.apply(R, v.x, [&](int64_t i, V ax) {
             V gi = ax - v.b[i];
@@ -234,7 +276,7 @@ __device__ int gpcg_solve(Team &T, const Rows &R, const Op &A, const Bounds<V> &
                 R.each([&](int64_t i) { v.p[i] = -proj_grad(v.x[i], v.g[i], B.l(i), B.h(i)); });
                 st.vec += 3;
                 if (!T.sync()) return ST_TIMEOUT;
-                V a1[1] = {zero};
+                Acc<V> a1[1];
                 double d1[1], oc[2];
                 A.apply(R, v.p, [&](int64_t i, V ap) { a1[0] += v.p[i] * ap; });
                 const double gp2 = st.gp2;
@@ -251,7 +293,7 @@ __device__ int gpcg_solve(Team &T, const Rows &R, const Op &A, const Bounds<V> &
             bool accepted = false;
             double d2[6], o2[5];
             for (int ls = 0; ls < 48 && st.spmv < C.max_spmv; ++ls) {
-                V a2[6] = {zero, zero, zero, zero, zero, zero};
+                Acc<V> a2[6];
                 const V va = (V)alpha;
                 R.each([&](int64_t i) {
                     V l = B.l(i), h = B.h(i), xi = v.x[i];
@@ -329,7 +371,7 @@ __device__ int gpcg_solve(Team &T, const Rows &R, const Op &A, const Bounds<V> &
                 st.vec += 8;
                 st.fl += 1;
                 if (!T.sync()) return ST_TIMEOUT;
-                V a3[2] = {zero, zero};
+                Acc<V> a3[2];
                 double d3[2];
                 A.apply(R, v.z, [&](int64_t i, V au) {
                     V wi = v.fm[i] ? au : zero;
@@ -349,7 +391,7 @@ __device__ int gpcg_solve(Team &T, const Rows &R, const Op &A, const Bounds<V> &
                 cg_take(cs, o3);
                 for (int k = 0; k < C.cg_max; ++k) {
                     const V va = (V)cs.alpha, vb = (V)cs.beta;
-                    V a4[4] = {zero, zero, zero, zero};   // gamma, delta, r'r, bound crossings
+                    Acc<V> a4[4];   // gamma, delta, r'r, bound crossings
                     const void *pf6[6] = {v.z, v.p, v.w, v.q, v.s, v.r};
                     R.each_pf(pf6, (int)sizeof(V), pf_on, [&](int64_t i) {
                         V pi = v.z[i] + vb * v.p[i];
@@ -417,7 +459,7 @@ __device__ int gpcg_solve(Team &T, const Rows &R, const Op &A, const Bounds<V> &
                 st.vec += 10;
                 st.fl += 1;
                 if (!T.sync()) return ST_TIMEOUT;
-                V a3[2] = {zero, zero};
+                Acc<V> a3[2];
                 double d3[2];
                 A.apply(R, mn, [&](int64_t i, V au) {
                     V wi = v.fm[i] ? au : zero;
@@ -439,7 +481,7 @@ __device__ int gpcg_solve(Team &T, const Rows &R, const Op &A, const Bounds<V> &
                 cg_take(cs, o3);
                 for (int k = 0; k < C.cg_max; ++k) {
                     const V va = (V)cs.alpha, vb = (V)cs.beta;
-                    V a4[4] = {zero, zero, zero, zero};   // gamma, delta, r'r, bound crossings
+                    Acc<V> a4[4];   // gamma, delta, r'r, bound crossings
                     A.apply(R, mc, [&](int64_t i, V an) {
                         V ni = v.fm[i] ? an : zero;
                         V di = v.dinv[i];
@@ -483,7 +525,7 @@ __device__ int gpcg_solve(Team &T, const Rows &R, const Op &A, const Bounds<V> &
                 }
             } else {
                 // textbook preconditioned CG
-                V a3[1] = {zero};
+                Acc<V> a3[1];
                 double d3[1];
                 R.each([&](int64_t i) {
                     V xi = v.x[i];
@@ -504,24 +546,30 @@ __device__ int gpcg_solve(Team &T, const Rows &R, const Op &A, const Bounds<V> &
                 if (!(rho > 0.0)) break;
                 double maxdec = 0.0;
                 for (int k = 0; k < C.cg_max; ++k) {
-                    V a4[1] = {zero};
+                    Acc<V> a4[1];
                     double d4[1];
                     A.apply(R, v.p, [&](int64_t i, V ap) {
                         V qi = v.fm[i] ? ap : zero;
                         v.q[i] = qi;
                         a4[0] += v.p[i] * qi;
                     });
-                    if (!team_sum(T, a4, d4)) return ST_TIMEOUT;
+                    // alpha = rho / p'q, computed once per block by warp 0
+                    double o4[2];
+                    if (!team_sum_scalar(T, a4, d4, o4, [&](const double (&d)[1], double (&r)[2]) {
+                            r[0] = d[0] > 0.0 ? 1.0 : 0.0;
+                            r[1] = rho / d[0];
+                        }))
+                        return ST_TIMEOUT;
                     ++st.spmv;
                     st.vec += 2;
                     st.fl += 2;
-                    if (!(d4[0] > 0.0)) break;
-                    const double alpha = rho / d4[0];
+                    if (!flag_set(o4[0])) break;
+                    const double alpha = o4[1];
                     const V va = (V)alpha;
-                    V a5[3] = {zero, zero, zero};
+                    Acc<V> a5[3];
                     double d5[3];
                     const void *pf5[5] = {v.s, v.p, v.r, v.q, v.dinv};
-                    R.each_pf(pf5, (int)sizeof(V), pf_on, [&](int64_t i) {
+                    auto upd = [&](int64_t i) {
                         V si = v.s[i] + va * v.p[i];
                         V ri = v.r[i] - va * v.q[i];
                         V zi = v.dinv[i] * ri;
@@ -534,20 +582,74 @@ __device__ int gpcg_solve(Team &T, const Rows &R, const Op &A, const Bounds<V> &
                             V xs = v.x[i] + si;
                             a5[2] += (xs < B.l(i) || xs > B.h(i)) ? one : zero;
                         }
-                    });
-                    if (!team_sum(T, a5, d5)) return ST_TIMEOUT;
+                    };
+                    const void *al6[6] = {v.s, v.p, v.r, v.q, v.dinv, v.z};
+                    if (!count_cross && aligned16(al6)) {
+                        constexpr int W = Pack<V>::W;
+                        R.each_chunk<W>([&](int64_t i, int cnt) {
+                            if (cnt < W) {
+                                for (int j = 0; j < cnt; ++j) upd(i + j);
+                                return;
+                            }
+                            V sv[W], pv[W], rv[W], qv[W], dv[W];
+                            ld_pack(v.s + i, sv);
+                            ld_pack(v.p + i, pv);
+                            ld_pack(v.r + i, rv);
+                            ld_pack(v.q + i, qv);
+                            ld_pack(v.dinv + i, dv);
+#pragma unroll
+                            for (int j = 0; j < W; ++j) {
+                                sv[j] = sv[j] + va * pv[j];
+                                rv[j] = rv[j] - va * qv[j];
+                                dv[j] = dv[j] * rv[j];
+                                a5[0] += rv[j] * dv[j];
+                                a5[1] += rv[j] * rv[j];
+                            }
+                            st_pack(v.s + i, sv);
+                            st_pack(v.r + i, rv);
+                            st_pack(v.z + i, dv);
+                        });
+                    } else {
+                        R.each_pf(pf5, (int)sizeof(V), pf_on, upd);
+                    }
+                    // stop test and beta = rho' / rho, once per block by warp 0
+                    double o5[3];
+                    const double md = maxdec;
+                    if (!team_sum_scalar(T, a5, d5, o5, [&](const double (&d)[3], double (&r)[3]) {
+                            const double dec = 0.5 * alpha * rho;
+                            const double mdn = dec > md ? dec : md;
+                            r[0] = ((count_cross && d[2] > 0.0) || dec <= C.eta2 * mdn || d[1] <= ftol2 || !(d[0] > 0.0))
+                                       ? 1.0
+                                       : 0.0;
+                            r[1] = d[0] / rho;
+                            r[2] = mdn;
+                        }))
+                        return ST_TIMEOUT;
                     ++st.cg;
                     st.vec += count_cross ? 9 : 8;
                     st.fl += 9;
-                    const double dec = 0.5 * alpha * rho;
-                    if (dec > maxdec) maxdec = dec;
-                    if ((count_cross && d5[2] > 0.0) || dec <= C.eta2 * maxdec || d5[1] <= ftol2 ||
-                        st.spmv >= C.max_spmv || !(d5[0] > 0.0))
-                        break;
-                    const V vb = (V)(d5[0] / rho);
+                    maxdec = o5[2];
+                    if (flag_set(o5[0]) || st.spmv >= C.max_spmv) break;
+                    const V vb = (V)o5[1];
                     rho = d5[0];
                     const void *pf2[2] = {v.z, v.p};
-                    R.each_pf(pf2, (int)sizeof(V), pf_on, [&](int64_t i) { v.p[i] = v.z[i] + vb * v.p[i]; });
+                    if (aligned16(pf2)) {
+                        constexpr int W = Pack<V>::W;
+                        R.each_chunk<W>([&](int64_t i, int cnt) {
+                            if (cnt < W) {
+                                for (int j = 0; j < cnt; ++j) v.p[i + j] = v.z[i + j] + vb * v.p[i + j];
+                                return;
+                            }
+                            V zv[W], pv[W];
+                            ld_pack(v.z + i, zv);
+                            ld_pack(v.p + i, pv);
+#pragma unroll
+                            for (int j = 0; j < W; ++j) pv[j] = zv[j] + vb * pv[j];
+                            st_pack(v.p + i, pv);
+                        });
+                    } else {
+                        R.each_pf(pf2, (int)sizeof(V), pf_on, [&](int64_t i) { v.p[i] = v.z[i] + vb * v.p[i]; });
+                    }
                     st.vec += 3;
                     st.fl += 2;
                     if (!T.sync()) return ST_TIMEOUT;
@@ -558,7 +660,7 @@ __device__ int gpcg_solve(Team &T, const Rows &R, const Op &A, const Bounds<V> &
             bool accepted = false;
             double d6[5], o6[3];
             for (int ls = 0; ls < 48; ++ls) {
-                V a6[5] = {zero, zero, zero, zero, zero};
+                Acc<V> a6[5];
                 const V va = (V)alpha;
                 R.each([&](int64_t i) {
                     V xi = v.x[i];

@@ -65,6 +65,7 @@ struct GridArgs {
     double *xprev;          // [n] c^(n-1) at the free nodes
     double *xprev2;         // [n] c^(n-2) (quadratic extrapolation)
     uint8_t *fmask;         // [n] face mask of the CG phases
+    int tma_slot_entries;   // FMT 3: 32 x the widest slice (slot size of the streamed operator)
 };
 
 // Initial iterate of a backward-Euler step: linear extrapolation of the last
@@ -131,14 +132,19 @@ __device__ bool step_outputs(Team &T, const Rows &R, const GridArgs &a, const do
 
 // One instantiation per (format, mode) so that each kernel carries only the
 // code of its own path (register allocation is per kernel).
-// TPB threads per block: 256 (several blocks per SM on large systems) or 512
-// (one block per SM on mid-size systems: one slice per warp, so the loads of
-// a pass are all in flight at once).
+// TPB threads per block: 256 (several blocks per SM), 512 (one block per SM
+// on mid-size systems: one slice per warp, so the loads of a pass are all in
+// flight at once) or 768 (one block of 24 warps per SM on large systems: the
+// warps of three 256-thread blocks with a third of the barrier arrivals and
+// reduction partials).
 // FMT: 0 = SELL, 1 = CSR (FP64), 2 = SELL with the block's slices of the
 // operator that the inner products use (FP64 A, or FP32 A in the mixed
 // modes) held in shared memory for the whole launch: staged once, then every
 // product reads its columns and values on chip and only gathers x from L2
-// (mid-size systems, whose slices per block fit in shared memory).
+// (mid-size systems, whose slices per block fit in shared memory);
+// 3 (mixed modes) = the FP32 operator of the inner products streamed through
+// shared memory by bulk asynchronous copies, D slices in flight per warp
+// (operators far larger than L2).
 template <int FMT, int MODE, int CGV, int TPB>
 __global__ void __launch_bounds__(TPB, TPB >= 512 ? 1 : mode_min_blocks(MODE)) k_solve_grid(GridArgs a) {
     __shared__ RedSmem sm;
@@ -149,6 +155,19 @@ __global__ void __launch_bounds__(TPB, TPB >= 512 ? 1 : mode_min_blocks(MODE)) k
     R.each([&](int64_t i) { x[i] = a.c_in[a.free_node[i]]; });
     SellF64Local Aloc{};
     SellF32DiffLocal A32loc{};
+    SellF32DiffTma A32tma{};
+    if constexpr (FMT == 3) {
+        static_assert(mode_mixed(MODE), "the streamed FP32 operator serves the mixed modes");
+        A32tma.n = a.A32.n;
+        A32tma.nslices = a.A32.nslices;
+        A32tma.sptr = a.A32.sptr;
+        A32tma.col = a.A32.col;
+        A32tma.val = a.A32.val;
+        A32tma.rsum = a.A32.rsum;
+        A32tma.slot_entries = a.tma_slot_entries;
+        A32tma.error = &a.bar->error;
+        A32tma.setup(op_smem);
+    }
     if constexpr (FMT == 2) {
         // stage entries [e0, e1) of this block's slices: columns, then values
         constexpr bool MIX = mode_mixed(MODE);
@@ -190,6 +209,10 @@ __global__ void __launch_bounds__(TPB, TPB >= 512 ? 1 : mode_min_blocks(MODE)) k
             MixedStats ms;
             if constexpr (FMT == 2)
                 status = mixed_solve<CGV, true>(T, R, a.A, A32loc, a.lo, a.hi, b, x, v, a.v32[9], a.v32[10],
+                                                 a.v32[11], v64, a.rtol * den, a.inner_rtol, a.max_ref,
+                                                 a.ctl.max_spmv, a.inner_cap, a.ctl, a.ctl, ms);
+            else if constexpr (FMT == 3)
+                status = mixed_solve<CGV, (TPB < 512)>(T, R, a.A, A32tma, a.lo, a.hi, b, x, v, a.v32[9], a.v32[10],
                                                  a.v32[11], v64, a.rtol * den, a.inner_rtol, a.max_ref,
                                                  a.ctl.max_spmv, a.inner_cap, a.ctl, a.ctl, ms);
             else
@@ -243,8 +266,10 @@ __global__ void __launch_bounds__(TPB, TPB >= 512 ? 1 : mode_min_blocks(MODE)) k
 
 using GridKernel = void (*)(GridArgs);
 
-// Internal format code of the shared-memory-resident SELL operator.
+// Internal format codes: the shared-memory-resident SELL operator, and the
+// FP32 SELL operator streamed through shared memory by bulk copies.
 constexpr int FMT_SELL_SMEM = 2;
+constexpr int FMT_SELL_TMA = 3;
 
 // Kernel of one mode for format fmt (NN_FMT_SELL / NN_FMT_CSR /
 // FMT_SELL_SMEM), CG variant cgv (0, 1, 2) and threads per block tpb (256,
@@ -253,5 +278,6 @@ GridKernel grid_kernel_steady(int fmt, int cgv, int tpb);
 GridKernel grid_kernel_transient(int fmt, int cgv, int tpb);
 GridKernel grid_kernel_mixed(int fmt, int cgv, int tpb);
 GridKernel grid_kernel_mixed_transient(int fmt, int cgv, int tpb);
+GridKernel grid_kernel_tma(int mode, int cgv, int tpb);
 
 }  // namespace nnqp

@@ -16,6 +16,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include "team.cuh"
+#include "tma.cuh"
 
 namespace nnqp {
 
@@ -208,12 +209,139 @@ struct SellF32DiffX {
 using SellF32Diff = SellF32DiffX<false>;
 using SellF32DiffLocal = SellF32DiffX<true>;
 
+// The FP32 difference-form operator of SellF32DiffX, streamed from global
+// memory through shared memory by bulk asynchronous copies (TMA) for
+// operators far larger than L2.  Each warp owns a ring of D slots in the
+// block's dynamic shared memory; its lane 0 copies the columns and values
+// of the warp's slice s + (D-1) nw (contiguous in the SELL layout) into the
+// next slot while the warp computes slice s from the current one, so every
+// warp keeps D-1 slices of the operator in flight without holding them in
+// registers.  The copies carry an evict-first L2 policy: the gathered vector
+// stays in L2 while the operator streams past it.  Slot and mbarrier phase
+// bookkeeping persists across products through a per-warp use counter in
+// shared memory.  A copy that does not complete within the bounded wait sets
+// the grid's error word (the host then reports NN_ERR_TIMEOUT), waits for
+// the warp's other copies in flight and skips the rest of the product.
+struct SellF32DiffTma {
+    static constexpr int D = 2;           // slots per warp
+    int64_t n, nslices;
+    const int64_t *__restrict__ sptr;
+    const int32_t *__restrict__ col;
+    const float *__restrict__ val;
+    const float *__restrict__ rsum;
+    int slot_entries;                     // 32 x the widest slice (even)
+    uint64_t *bars;                       // [warps][D] (shared memory)
+    unsigned *uses;                       // [warps] slots consumed so far (shared memory)
+    unsigned char *buf;                   // [warps][D][slot_entries * 8] (shared memory)
+    int *error;                           // grid error word (global memory)
+
+    // Shared memory a block of `warps` warps needs: mbarriers (512 B) and
+    // use counters (128 B) in a 1 KB header, then the slots.
+    static constexpr int kHeader = 1024;
+    __host__ __device__ static size_t smem_bytes(int warps, int slot_entries) {
+        return kHeader + (size_t)warps * D * slot_entries * 8;
+    }
+
+    // Carves the block's shared memory and initialises its mbarriers
+    // (every thread calls it; ends with __syncthreads).
+    __device__ void setup(unsigned char *smem) {
+        const int nw = blockDim.x >> 5;
+        bars = reinterpret_cast<uint64_t *>(smem);
+        uses = reinterpret_cast<unsigned *>(smem + 8 * kMaxWarps * D);
+        buf = smem + kHeader;
+        if (threadIdx.x < (unsigned)(nw * D)) mbar_init(bars + threadIdx.x, 1);
+        if (threadIdx.x < (unsigned)nw) uses[threadIdx.x] = 0;
+        mbar_init_fence();
+        __syncthreads();
+    }
+
+    template <class Epi>
+    __device__ void apply(const Rows &R, const float *x, Epi &&epi) const {
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+        const size_t slot_bytes = (size_t)slot_entries * 8;
+        uint64_t *wb = bars + warp * D;
+        unsigned char *wbuf = buf + (size_t)warp * D * slot_bytes;
+        const uint64_t pol = l2_evict_first_policy();
+        const unsigned base = uses[warp];
+        const int64_t first = R.s0 + warp;
+        auto issue = [&](int64_t s, unsigned u) {
+            const int d = (int)(u % D);
+            const int64_t e0 = __ldg(sptr + s), e1 = __ldg(sptr + s + 1);
+            const unsigned ne = (unsigned)(e1 - e0);   // 32 x even width: a multiple of 64 entries
+            unsigned char *dst = wbuf + (size_t)d * slot_bytes;
+            fence_proxy_async_smem();
+            mbar_arrive_expect_tx(wb + d, ne * 8);
+            if (ne > 0) {
+                bulk_copy_g2s(dst, col + e0, ne * 4, wb + d, pol);
+                bulk_copy_g2s(dst + (size_t)slot_entries * 4, val + e0, ne * 4, wb + d, pol);
+            }
+        };
+        if (lane == 0)
+            for (int d = 0; d < D - 1; ++d)
+                if (first + (int64_t)d * nw < R.s1) issue(first + (int64_t)d * nw, base + d);
+        __syncwarp();
+        unsigned k = 0;
+        for (int64_t s = first; s < R.s1; s += nw, ++k) {
+            const unsigned u = base + k;
+            if (lane == 0 && s + (int64_t)(D - 1) * nw < R.s1) issue(s + (int64_t)(D - 1) * nw, u + D - 1);
+            if (!mbar_wait_bounded(wb + (u % D), (u / D) & 1u)) {
+                if (lane == 0) atomicCAS(error, 0, 7 /* NN_ERR_TIMEOUT */);
+                for (unsigned j = 1; j < (unsigned)D && s + (int64_t)j * nw < R.s1; ++j)
+                    mbar_wait_bounded(wb + ((u + j) % D), ((u + j) / D) & 1u);
+                k += 1;
+                for (int64_t t = s + nw; t < R.s1 && t <= s + (int64_t)(D - 1) * nw; t += nw) ++k;
+                break;
+            }
+            const unsigned char *sb = wbuf + (size_t)(u % D) * slot_bytes;
+            const int w = (int)((__ldg(sptr + s + 1) - __ldg(sptr + s)) >> 5);
+            const int2 *c2 = reinterpret_cast<const int2 *>(sb) + lane;
+            const float2 *v2 = reinterpret_cast<const float2 *>(sb + (size_t)slot_entries * 4) + lane;
+            const int64_t i = s * 32 + lane;
+            const float xi = i < n ? x[i] : 0.0f;
+            float a0 = 0.0f, a1 = 0.0f;
+            int kk = 0;
+            for (; kk + 8 <= w; kk += 8) {
+                int2 c[4];
+                float2 v[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    c[j] = c2[16 * (kk + 2 * j)];
+                    v[j] = v2[16 * (kk + 2 * j)];
+                }
+                float xv[8];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    xv[2 * j] = x[c[j].x];
+                    xv[2 * j + 1] = x[c[j].y];
+                }
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    a0 = fmaf(v[j].x, xv[2 * j] - xi, a0);
+                    a1 = fmaf(v[j].y, xv[2 * j + 1] - xi, a1);
+                }
+            }
+            for (; kk < w; kk += 2) {
+                const int2 c = c2[16 * kk];
+                const float2 v = v2[16 * kk];
+                a0 = fmaf(v.x, x[c.x] - xi, a0);
+                a1 = fmaf(v.y, x[c.y] - xi, a1);
+            }
+            if (i < n) epi(i, fmaf(__ldg(rsum + i), xi, a0 + a1));
+            __syncwarp();
+        }
+        __syncwarp();
+        if (lane == 0) uses[warp] = base + k;
+        __syncwarp();
+    }
+};
+
 // Whether an operator streams through L2 (large systems): the vector passes
 // of its solves prefetch their next slices too.
 template <bool L>
 __device__ __forceinline__ bool op_streams(const SellF64X<L> &A) { return A.stream; }
 template <bool L>
 __device__ __forceinline__ bool op_streams(const SellF32DiffX<L> &A) { return A.stream; }
+__device__ __forceinline__ bool op_streams(const SellF32DiffTma &) { return true; }
 template <class Op>
 __device__ __forceinline__ bool op_streams(const Op &) { return false; }
 

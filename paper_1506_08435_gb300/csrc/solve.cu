@@ -180,6 +180,15 @@ namespace {
 constexpr double kStreamBytes = 48.0 * (1 << 20);
 // Most shared memory a block's staged operator slices may take.
 constexpr size_t kSmemOperatorBytes = 192 * 1024;
+// Shared-memory budget of the streamed FP32 operator's slots per block
+// (8 warps x 2 slots x 32 rows x 16 entries x 8 bytes, plus a 1 KB header).
+constexpr size_t kTmaSmemBytes = 66 * 1024;
+// The same for one 768-thread block per SM (24 warps).
+constexpr size_t kTmaSmemBytesLarge = 196 * 1024;
+// Threads per block of the large-system grids (one block per SM): FP64,
+// and mixed precision.
+constexpr int kLargeThreads = 768;
+constexpr int kLargeThreadsMixed = 512;
 // Threads per block of the projected L-BFGS kernel (128 was measured too:
 // faster on the 50^2 problem, slower on the 40^3 transient run).
 constexpr int kLbfgsThreads = 256;
@@ -395,14 +404,22 @@ nn_status plan_build(nn_system *s, const nn_solve_opts *o, int mode, int nsteps,
     const int64_t slices = s->A64.nslices;
     int tpb = kSolveThreads;
     const bool driver = lbfgs || tron;   // solvers with a kernel of their own
+    // Large systems (more than 32 slices per SM) run one 768-thread block
+    // per SM with the textbook CG form: the warps of three 256-thread blocks,
+    // a third of the barrier arrivals and reduction partials.  (Served
+    // requests of that size take the whole device, so they may too.)
+    const bool large = !driver && (slices > (int64_t)4 * 8 * sms || force_large);
     if (!driver && slices <= (int64_t)4 * 8 * sms && slices > (int64_t)8 * sms / 2) tpb = 512;
-    if (const char *e = getenv("NNQP_GRID_THREADS")) tpb = atoi(e);
     if (!driver && (force_tpb == 256 || force_tpb == 512)) tpb = force_tpb;
+    // Mixed solves of that size run 512-thread blocks (one per SM): their
+    // FP32 inner solve, inlined, needs the larger register budget.
+    if (large && a.ctl.cg_variant == 0 && fmt == NN_FMT_SELL && force_tpb != 512)
+        tpb = mixed ? kLargeThreadsMixed : kLargeThreads;
     if (force_large) {
-        tpb = kSolveThreads;
         a.A.stream = true;
         a.A32.stream = true;
     }
+    if (const char *e = getenv("NNQP_GRID_THREADS")) tpb = atoi(e);
     GridKernel kern = lbfgs ? k_lbfgs_grid : tron ? k_tron_grid : grid_kernel(mode, fmt, a.ctl.cg_variant, tpb);
     if (!kern && !driver && tpb != kSolveThreads) {
         tpb = kSolveThreads;
@@ -425,7 +442,7 @@ nn_status plan_build(nn_system *s, const nn_solve_opts *o, int mode, int nsteps,
     const int64_t spread = std::max<int64_t>(by_rows, (slices + 3) / 4);
     int want = (int)std::min<int64_t>(spread, slices <= (int64_t)4 * 8 * sms ? (int64_t)sms : (int64_t)maxg);
     want = std::min(want, maxg);
-    if (force_large) want = maxg;
+    if (large) want = maxg;
     if (o->grid_blocks > 0) want = std::min(o->grid_blocks, maxg);
     want = std::max(want, 1);
     // Mid-size SELL solves keep each block's slices of the operator of the
@@ -461,6 +478,42 @@ nn_status plan_build(nn_system *s, const nn_solve_opts *o, int mode, int nsteps,
             }
         }
         cudaGetLastError();   // a refused attribute leaves the plain kernel in use
+    }
+    // Large mixed solves stream the FP32 operator of their inner products
+    // through shared memory with bulk asynchronous copies (FMT 3), when the
+    // slots of 8 warps fit the fixed budget and at least two blocks stay
+    // resident per SM.  NNQP_TMA_OP=0 keeps the load-based operator.
+    const char *tma_env = getenv("NNQP_TMA_OP");
+    if (!driver && fmt == NN_FMT_SELL && mixed && (tpb == kSolveThreads || tpb == kLargeThreadsMixed) &&
+        a.ctl.cg_variant == 0 && a.A32.stream && dyn_smem == 0 && !(tma_env && tma_env[0] == '0')) {
+        if (s->sptr_host.empty()) {
+            s->sptr_host.resize((size_t)slices + 1);
+            NN_CUDA_TRY(cudaMemcpyAsync(s->sptr_host.data(), s->A64.sptr, sizeof(int64_t) * (slices + 1),
+                                        cudaMemcpyDeviceToHost, st));
+            NN_CUDA_TRY(cudaStreamSynchronize(st));
+        }
+        int64_t wmax = 0;
+        for (int64_t k = 0; k < slices; ++k)
+            wmax = std::max<int64_t>(wmax, (s->sptr_host[(size_t)k + 1] - s->sptr_host[(size_t)k]) >> 5);
+        const int se = (int)(32 * std::max<int64_t>(wmax, 2));
+        const size_t bytes = SellF32DiffTma::smem_bytes(tpb / 32, se);
+        GridKernel kt = grid_kernel(mode, FMT_SELL_TMA, 0, tpb);
+        const size_t budget = tpb == kLargeThreadsMixed ? kTmaSmemBytesLarge : kTmaSmemBytes;
+        if (kt && bytes <= budget &&
+            cudaFuncSetAttribute((const void *)kt, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)budget) ==
+                cudaSuccess) {
+            int per = 0;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kt, tpb, bytes);
+            if (per * tpb >= 2 * kSolveThreads) {
+                const bool full_grid = want >= maxg;
+                kern = kt;
+                dyn_smem = bytes;
+                maxg = per * sms;
+                want = full_grid ? maxg : std::min(want, maxg);
+                a.tma_slot_entries = se;
+            }
+        }
+        cudaGetLastError();   // a refused attribute leaves the load-based kernel in use
     }
     // NNQP_TEST_STALL_BARRIER=1 makes the grid barrier wait for one block
     // that does not exist, so every wait runs into its time limit: the test of

@@ -12,9 +12,11 @@ GridKernel grid_kernel_mixed(int fmt, int cgv, int tpb) {
             default: return nullptr;
         }
     }
+    if (fmt == FMT_SELL_TMA) return grid_kernel_tma(MODE_MIXED, cgv, tpb);
     if (fmt != NN_FMT_SELL) return nullptr;
     if (tpb == 512) {
         switch (cgv) {
+            case 0: return k_solve_grid<0, MODE_MIXED, 0, 512>;
             case 1: return k_solve_grid<0, MODE_MIXED, 1, 512>;
             case 2: return k_solve_grid<0, MODE_MIXED, 2, 512>;
             default: return nullptr;

@@ -12,6 +12,7 @@ GridKernel grid_kernel_mixed_transient(int fmt, int cgv, int tpb) {
             default: return nullptr;
         }
     }
+    if (fmt == FMT_SELL_TMA) return grid_kernel_tma(MODE_MIXED_TR, cgv, tpb);
     if (fmt != NN_FMT_SELL) return nullptr;
     if (tpb == 512) {
         switch (cgv) {

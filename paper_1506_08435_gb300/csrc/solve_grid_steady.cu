@@ -20,6 +20,7 @@ GridKernel grid_kernel_steady(int fmt, int cgv, int tpb) {
             default: return nullptr;
         }
     }
+    if (tpb == 768) return cgv == 0 ? k_solve_grid<0, MODE_STEADY, 0, 768> : nullptr;
     if (tpb == 512) {
         switch (cgv) {
             case 1: return k_solve_grid<0, MODE_STEADY, 1, 512>;

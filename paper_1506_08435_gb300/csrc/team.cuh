@@ -151,15 +151,19 @@ __device__ __forceinline__ void warp_stage(const double (&v)[K], RedSmem &sm) {
 // Cross-warp stage: the per-warp totals sm.warp[w][k] (w < nw) are summed in
 // a fixed butterfly order by warp 0 and stored to sm.bcast[k].  Lanes are
 // packed (k, w) so that one FP64 instruction serves 32 / nw entries.
+// A block whose warp count is not a power of two (24 warps of 768 threads)
+// is summed as the next power of two with zero totals for the missing warps.
 template <int K>
 __device__ __forceinline__ void warp0_sum_warps(RedSmem &sm) {
     const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    const int per = 32 / nw;                  // entries per warp instruction
-    const int k_in = lane / nw, w = lane % nw;
+    int np = 1;
+    while (np < nw) np <<= 1;
+    const int per = 32 / np;                  // entries per warp instruction
+    const int k_in = lane / np, w = lane % np;
     for (int k0 = 0; k0 < K; k0 += per) {
         const int k = k0 + k_in;
-        double t = (k < K && k_in < per) ? sm.warp[w][k] : 0.0;
-        for (int o = nw >> 1; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        double t = (k < K && k_in < per && w < nw) ? sm.warp[w][k] : 0.0;
+        for (int o = np >> 1; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
         if (w == 0 && k < K && k_in < per) sm.bcast[k] = t;
     }
 }
@@ -206,35 +210,39 @@ struct GridTeam {
     // (its block's writes become visible first) and polls the counter with
     // acquire loads, for at most timeout_ns; a wait that runs out sets the
     // error word, and a block that sees the error word set leaves as well.
+    // Arrival and bounded wait of the barrier numbered wait_id, by thread 0
+    // of the block (after the block's writes it must publish); 1 = passed.
+    __device__ int arrive_and_wait() {
+        int ok = 1;
+        const unsigned long long target = (unsigned long long)wait_id * (unsigned long long)nblocks;
+        red_release_add_u64(&bar->count, 1ULL);
+        unsigned spins = 0;
+        unsigned long long t0 = 0;
+        while (ld_acquire_u64(&bar->count) < target) {
+            ++spins;
+            if ((spins & 63u) == 0) {
+                if (ld_relaxed_i32(&bar->error)) {
+                    ok = 0;
+                    break;
+                }
+                const unsigned long long now = global_ns();
+                if (t0 == 0) {
+                    t0 = now;
+                } else if (now - t0 > timeout_ns) {
+                    if (atomicCAS(&bar->error, 0, 7 /* NN_ERR_TIMEOUT */) == 0) bar->where = wait_id;
+                    ok = 0;
+                    break;
+                }
+            }
+            if (spins > 256) __nanosleep(32);
+        }
+        return ok;
+    }
+
     __device__ bool sync() {
         __syncthreads();
         ++wait_id;
-        if (threadIdx.x == 0) {
-            int ok = 1;
-            const unsigned long long target = (unsigned long long)wait_id * (unsigned long long)nblocks;
-            red_release_add_u64(&bar->count, 1ULL);
-            unsigned spins = 0;
-            unsigned long long t0 = 0;
-            while (ld_acquire_u64(&bar->count) < target) {
-                ++spins;
-                if ((spins & 63u) == 0) {
-                    if (ld_relaxed_i32(&bar->error)) {
-                        ok = 0;
-                        break;
-                    }
-                    const unsigned long long now = global_ns();
-                    if (t0 == 0) {
-                        t0 = now;
-                    } else if (now - t0 > timeout_ns) {
-                        if (atomicCAS(&bar->error, 0, 7 /* NN_ERR_TIMEOUT */) == 0) bar->where = wait_id;
-                        ok = 0;
-                        break;
-                    }
-                }
-                if (spins > 256) __nanosleep(32);
-            }
-            sm->flag = ok;
-        }
+        if (threadIdx.x == 0) sm->flag = arrive_and_wait();
         __syncthreads();
         return sm->flag != 0;
     }
@@ -245,13 +253,19 @@ struct GridTeam {
         warp_stage<K>(v, *sm);
         __syncthreads();
         slot ^= 1;
+        ++wait_id;
         double *P = partials + (size_t)slot * kMaxRed * nblocks;
+        // warp 0 sums the warps, publishes the block's partials and passes
+        // the grid barrier; the other warps wait for it at one block barrier
         if (warp == 0) {
             warp0_sum_warps<K>(*sm);
             __syncwarp();
             for (int k = lane; k < K; k += 32) P[(size_t)k * nblocks + blockIdx.x] = sm->bcast[k];
+            __syncwarp();
+            if (lane == 0) sm->flag = arrive_and_wait();
         }
-        if (!sync()) return false;
+        __syncthreads();
+        if (sm->flag == 0) return false;
         if (K <= nw) {
             // warp k sums the per-block partials of entry k; the loads of
             // different entries are in flight together
@@ -306,9 +320,10 @@ struct GridTeam {
             }
         }
         __syncthreads();
+        // (no barrier after the copy: the next writer of bcast or flag is
+        // behind the next reduction's or barrier's first block barrier)
 #pragma unroll
         for (int k = 0; k < K; ++k) v[k] = sm->bcast[k];
-        __syncthreads();
         return true;
     }
 };
@@ -383,6 +398,19 @@ struct Rows {
             if (i < n) f(i);
         }
     }
+    // Element-wise pass over the block's rows with W consecutive rows per
+    // thread: f(i, cnt) handles rows i .. i + cnt - 1 (cnt = W except at the
+    // end of the system), so that it can move them with one vector access
+    // per array.  Each access then carries W times the bytes of a row-wise
+    // pass, which keeps more of a streaming pass in flight per warp.  (Only
+    // for passes with a barrier on both sides: the rows a thread touches
+    // differ from the row-per-lane passes.)
+    template <int W, class F>
+    __device__ __forceinline__ void each_chunk(F &&f) const {
+        const int64_t r0 = s0 * 32, r1 = s1 * 32 < n ? s1 * 32 : n;
+        for (int64_t i = r0 + (int64_t)threadIdx.x * W; i < r1; i += (int64_t)blockDim.x * W)
+            f(i, r1 - i < W ? (int)(r1 - i) : W);
+    }
     // The same pass with an L2 prefetch of the warp's next slice of the NP
     // vectors it reads (esize bytes per entry), issued by one lane per
     // 128-byte line: on large systems a warp then has the next rows' loads in
@@ -404,6 +432,47 @@ struct Rows {
         }
     }
 };
+
+// W consecutive entries of a vector of V moved by one vector access (16 bytes).
+template <typename V>
+struct Pack;
+template <>
+struct Pack<float> {
+    static constexpr int W = 4;
+    using T = float4;
+};
+template <>
+struct Pack<double> {
+    static constexpr int W = 2;
+    using T = double2;
+};
+
+template <typename V>
+__device__ __forceinline__ void ld_pack(const V *p, V (&o)[Pack<V>::W]) {
+    const typename Pack<V>::T t = *reinterpret_cast<const typename Pack<V>::T *>(p);
+    const V *e = reinterpret_cast<const V *>(&t);
+#pragma unroll
+    for (int k = 0; k < Pack<V>::W; ++k) o[k] = e[k];
+}
+
+template <typename V>
+__device__ __forceinline__ void st_pack(V *p, const V (&o)[Pack<V>::W]) {
+    typename Pack<V>::T t;
+    V *e = reinterpret_cast<V *>(&t);
+#pragma unroll
+    for (int k = 0; k < Pack<V>::W; ++k) e[k] = o[k];
+    *reinterpret_cast<typename Pack<V>::T *>(p) = t;
+}
+
+// True if every pointer is 16-byte aligned (the packed passes need it; the
+// rows of a block start at a multiple of 32).
+template <int K>
+__device__ __forceinline__ bool aligned16(const void *const (&p)[K]) {
+    uintptr_t o = 0;
+#pragma unroll
+    for (int k = 0; k < K; ++k) o |= reinterpret_cast<uintptr_t>(p[k]);
+    return (o & 15) == 0;
+}
 
 __host__ __device__ __forceinline__ Rows rows_of_block(int64_t n, int64_t nslices, int block, int nblocks) {
     int64_t per = (nslices + nblocks - 1) / nblocks;

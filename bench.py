@@ -412,10 +412,10 @@ def run_steady(P, torch, args, rank, dim):
     else:
         spec = I.config1_steady_2d(n=args.n or 50)
     dev = torch.device("cuda")
-    prec = P.NN_PREC_MIXED if args.cur_precision == "mixed" else P.NN_PREC_FP64
+    prec = {"mixed": P.NN_PREC_MIXED, "auto": P.NN_PREC_AUTO}.get(args.cur_precision, P.NN_PREC_FP64)
     opts = P.solve_opts(rtol=args.rtol, precision=prec, max_iter=args.max_iter,
                         solver=solver_code(P, args), ksp_rtol=args.ksp_rtol)
-    aopts = P.assemble_opts(build_mixed=1 if prec == P.NN_PREC_MIXED else 0)
+    aopts = P.assemble_opts(build_mixed=1 if prec != P.NN_PREC_FP64 else 0)
     prob = P.Problem(spec, device=dev)
     c = torch.zeros(spec.n_nodes, dtype=torch.float64, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
@@ -590,71 +590,126 @@ def run_batch(P, torch, args, rank):
 
 
 def run_serve(P, torch, args, rank):
+    """The serving stream as specified: Poisson arrivals at `rate` for
+    `duration` s (seed 2015); arrival r carries request r, seeded (2015, r)
+    (nn_inputs.serve_request).  The client sheds load like a bounded queue:
+    an arrival that finds `queue` requests waiting (in the server's queue or
+    still being generated) is refused and counted; otherwise its payload is
+    generated by a pool of spawned processes and submitted.  Server latency is
+    submit -> result; the client's generation time is reported beside it."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    from collections import deque
     rate, duration = args.rate, args.duration
     arrivals = I.serve_arrivals(rate, duration)
-    pool = [I.serve_request(r) for r in range(args.pool)]
-    probs = [P.Problem(sp) for sp in pool]
     budget = int(args.budget_gb * (1 << 30))
-    sopts = P.solve_opts(precision=P.NN_PREC_MIXED if args.precision == "mixed" else P.NN_PREC_FP64)
+    prec = {"mixed": P.NN_PREC_MIXED, "auto": P.NN_PREC_AUTO}.get(args.cur_precision, P.NN_PREC_FP64)
+    sopts = P.solve_opts(precision=prec)
+    workers = max(2, min(12, (os.cpu_count() or 4) - 2))
+    gen = cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn"))
+    list(gen.map(I.serve_request, range(workers)))          # start the workers
+    # warm-up: one small and one large request through a server of its own
     sv = P.nn_serve_create(budget, P.serve_opts(max_inflight=args.inflight, queue_capacity=args.queue, solve=sopts))
-    # warm-up: one request of each kind
-    for k in range(min(2, len(probs))):
-        rid = P.nn_serve_submit(sv, probs[k])
+    for r in (0, 4):
+        sp = I.serve_request(r)
+        rid = P.nn_serve_submit(sv, P.Problem(sp))
         P.nn_serve_drain(sv)
-        P.nn_serve_poll(sv, rid, np.zeros(pool[k].n_nodes))
+        P.nn_serve_poll(sv, rid, np.zeros(sp.n_nodes))
     P.nn_serve_destroy(sv)
-    # a bounded queue: past saturation, arrivals are refused (counted) instead
-    # of piling up, so the drain after the arrival window stays short
     sv = P.nn_serve_create(budget, P.serve_opts(max_inflight=args.inflight, queue_capacity=args.queue, solve=sopts))
     l0 = P.kernel_launches()
-    ids = []
+    pending = deque()          # (r, arrival time, future) in arrival order
+    ids, kept, refused, late, gen_s = [], {}, 0, 0, []
+    keep_first = 32
+
+    def submit_ready(block=False):
+        nonlocal late
+        while pending and (block or pending[0][2].done()):
+            r, ta, fut = pending.popleft()
+            sp = fut.result()
+            gen_s.append(time.perf_counter() - t0 - ta)
+            try:
+                ids.append((P.nn_serve_submit(sv, P.Problem(sp)), r, sp.n_nodes))
+                if len(kept) < keep_first:
+                    kept[r] = sp
+            except P.NnError:
+                late += 1
+
     t0 = time.perf_counter()
-    for k, ta in enumerate(arrivals):
-        now = time.perf_counter() - t0
-        if ta > now:
-            time.sleep(ta - now)
-        try:
-            ids.append((P.nn_serve_submit(sv, probs[k % len(probs)]), k % len(probs)))
-        except P.NnError:
-            pass
+    for r, ta in enumerate(arrivals):
+        while True:
+            submit_ready()
+            now = time.perf_counter() - t0
+            if now >= ta:
+                break
+            time.sleep(min(ta - now, 0.002))
+        if P.nn_serve_stats(sv)["queued"] + len(pending) >= args.queue:
+            refused += 1
+            continue
+        pending.append((r, ta, gen.submit(I.serve_request, r)))
+    submit_ready(block=True)
+    window = time.perf_counter() - t0
     P.nn_serve_drain(sv)
     wall = time.perf_counter() - t0
     st = P.nn_serve_stats(sv)
-    ok, failed = 0, []
-    for rid, k in ids:
+    ok, failed, fallbacks, kkt_max = 0, [], 0, 0.0
+    for rid, r, nn in ids:
         try:
-            info = P.nn_serve_poll(sv, rid, np.zeros(pool[k].n_nodes))
+            info = P.nn_serve_poll(sv, rid, np.zeros(nn))
         except P.NnError as e:
             failed.append(str(e))
             continue
         ok += info is not None and info["status"] == 0
+        if info is not None:
+            fallbacks += int(info["fp64_fallback"])
+            kkt_max = max(kkt_max, info["kkt_rel"])
     P.nn_serve_destroy(sv)
+    gen.shutdown()
     launches = P.kernel_launches() - l0
-    # the plain path for comparison: the first requests of the pool, each
-    # assembled and solved alone in FP64 (nn_assemble + nn_qp_solve), one after another
+    # the plain FP64 path on the first served requests: each assembled from
+    # host arrays and solved alone by nn_qp_solve in FP64, one after another
     dev = torch.device("cuda")
-    seq_n = min(args.pool, 32)
     fp64 = P.solve_opts(precision=P.NN_PREC_FP64)
     torch.cuda.synchronize()
     t1 = time.perf_counter()
-    for sp in pool[:seq_n]:
-        s_ = P.nn_assemble(P.Problem(sp, device=dev))
+    for sp in kept.values():
+        s_ = P.nn_assemble(P.Problem(sp), P.assemble_opts())
         c_ = torch.zeros(sp.n_nodes, dtype=torch.float64, device=dev)
         P.nn_qp_solve(s_, c_, fp64)
         c_.cpu()
         del s_
     seq_s = time.perf_counter() - t1
-    served_work = sum(pool[k].n_nodes for _, k in ids) / max(len(ids), 1)
-    sequential = {"value": seq_n / seq_s, "unit": "solves/s", "requests": seq_n,
-                  "mean_nodes": float(np.mean([sp.n_nodes for sp in pool[:seq_n]])),
-                  "served_mean_nodes": served_work,
-                  "how": "first %d requests of the payload pool, copied from host, assembled and solved alone in "
-                         "FP64 one after another" % seq_n}
-    return dict(stats=st, wall=wall, offered=len(arrivals), ok=ok, failed=len(failed), sequential=sequential,
+    sequential = {"value": len(kept) / seq_s if kept else None, "unit": "solves/s", "requests": len(kept),
+                  "mean_nodes": float(np.mean([sp.n_nodes for sp in kept.values()])) if kept else None,
+                  "served_mean_nodes": float(np.mean([nn for _, _, nn in ids])) if ids else None,
+                  "how": "the first %d served requests, copied from host, assembled and solved alone in FP64 one "
+                         "after another (nn_assemble + nn_qp_solve)" % len(kept)}
+    return dict(stats=st, wall=wall, window=window, offered=len(arrivals), submitted=len(ids), refused=refused,
+                fallbacks=fallbacks, kkt_max=kkt_max,
+                late=late, ok=ok, failed=len(failed), sequential=sequential, gen_mean_s=float(np.mean(gen_s)) if gen_s else 0.0,
                 first_failure=failed[0] if failed else None, launches=launches,
-                config={"workload": "serve_poisson%g_for%gs" % (rate, duration), "payload_pool": args.pool,
+                config={"workload": "serve_poisson%g_for%gs" % (rate, duration), "requests": "request r seeded (2015, r)",
                         "max_inflight": args.inflight, "queue_capacity": args.queue, "budget_gb": args.budget_gb,
-                        "precision": args.precision})
+                        "precision": args.cur_precision, "client_workers": workers})
+
+
+def serving_object(r, args):
+    st = r["stats"]
+    return {"metric": "serving p50/p99 latency (submit -> result)", "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
+            "mean_ms": st["mean_ms"], "solves_per_s": st["solves_per_s"], "offered": r["offered"],
+            "offered_per_s": args.rate, "duration_s": args.duration, "submitted": r["submitted"],
+            "refused_at_arrival": r["refused"], "refused_at_submit": r["late"], "completed": st["completed"],
+            "ok": r["ok"], "failed": st["failed"], "first_failure": r["first_failure"], "window_s": r["window"],
+            "max_kkt_rel": r["kkt_max"], "fp64_fallbacks": r["fallbacks"],
+            "wall_s": r["wall"], "saturated": r["refused"] > 0 or st["solves_per_s"] < 0.95 * args.rate,
+            "client_generation_mean_s": r["gen_mean_s"], "bytes_peak_measured": st["bytes_peak"],
+            "bytes_reserved_peak": st["bytes_reserved_peak"], "estimate_overruns": st["estimate_overruns"],
+            "estimate_max_ratio": st["estimate_max_ratio"], "inflight_peak": st["inflight_peak"],
+            "dtype": {"mixed": "f32+f64", "auto": "f32+f64 where the FP32 operator exceeds 48 MB, else f64"}.get(
+                args.cur_precision, "f64"), "gpu_launches": r["launches"],
+            "sequential_fp64": r["sequential"],
+            "vs_sequential_fp64": (st["solves_per_s"] / r["sequential"]["value"]) if r["sequential"]["value"] else None,
+            "config": r["config"]}
 
 
 def main():
@@ -665,7 +720,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="steady3d",
                     choices=["transient3d", "steady3d", "steady2d", "batch", "serve", "cube_hole"])
-    ap.add_argument("--precision", default="auto", choices=["auto", "fp64", "mixed", "both"],
+    ap.add_argument("--precision", default="default", choices=["default", "auto", "fp64", "mixed", "both"],
                     help="auto: both for steady3d (FP64 line + mixed object), fp64 otherwise")
     ap.add_argument("--mass", default="consistent", choices=["consistent", "lumped"],
                     help="capacity matrix of the transient workload")
@@ -678,8 +733,10 @@ def main():
     ap.add_argument("--rtol", type=float, default=1e-10)
     ap.add_argument("--max-iter", type=int, default=200000)
     ap.add_argument("--rate", type=float, default=200.0)
-    ap.add_argument("--duration", type=float, default=10.0)
-    ap.add_argument("--pool", type=int, default=64)
+    ap.add_argument("--duration", type=float, default=60.0)
+    ap.add_argument("--serve-precision", default="auto", choices=["fp64", "mixed", "auto"],
+                    help="precision of the serving run attached to the default line")
+    ap.add_argument("--no-serving", action="store_true", help="default workload: skip the serving run")
     ap.add_argument("--inflight", type=int, default=8)
     ap.add_argument("--queue", type=int, default=64)
     ap.add_argument("--budget-gb", type=float, default=120.0)
@@ -693,9 +750,11 @@ def main():
     hbm_peak = pk["hbm_gbs"] if pk else FALLBACK_HBM
     peak_src = "measured (MEASURED_PEAKS.json hbm_gbs)" if pk else "fallback"
 
-    if args.workload == "steady3d" and args.precision == "auto":
+    if args.workload == "serve" and args.precision == "default":
+        args.precision = args.serve_precision
+    if args.workload == "steady3d" and args.precision == "default":
         args.precision = "both"
-    elif args.precision == "auto":
+    elif args.precision == "default":
         args.precision = "fp64"
     if args.precision == "both" and args.workload != "steady3d":
         args.precision = "fp64"
@@ -735,6 +794,10 @@ def main():
         line["mixed"] = sub
         line["vs_plain_fp64"] = m["value"] / line["value"]
         line["precision_note"] = "the line is the plain FP64 solve; \"mixed\" is the same workload in mixed precision"
+    if args.workload == "steady3d" and not args.no_serving and not args.n:
+        # the serving stream (config 5) on the same GPU, reported beside the line
+        args.cur_precision = args.serve_precision
+        line["serving"] = serving_object(run_serve(P, torch, args, rank), args)
     if rank == 0 and not args.no_cpu_baseline:
         v, cores, desc = oracle_sample(args.workload, n=args.n or None, lumped=args.mass == "lumped")
         if v is not None:
@@ -859,22 +922,14 @@ def result_line(r, args, prec, dist, ws, hbm_peak, peak_src):
 
 
 def serve_line(P, torch, args, rank, ws):
+    args.cur_precision = args.precision
     r = run_serve(P, torch, args, rank)
-    st = r["stats"]
     if rank == 0:
-        print(json.dumps({"metric": "serving p50/p99 latency", "value": st["p50_ms"], "unit": "ms",
-                          "p99_ms": st["p99_ms"], "mean_ms": st["mean_ms"], "solves_per_s": st["solves_per_s"],
-                          "offered": r["offered"], "offered_per_s": args.rate, "completed": st["completed"],
-                          "ok": r["ok"], "failed": st["failed"], "first_failure": r["first_failure"],
-                          "rejected": st["rejected"], "wall_s": r["wall"],
-                          "saturated": st["rejected"] > 0 or st["solves_per_s"] < 0.95 * args.rate,
-                          "bytes_peak_measured": st["bytes_peak"], "bytes_reserved_peak": st["bytes_reserved_peak"],
-                          "estimate_overruns": st["estimate_overruns"],
-                          "estimate_max_ratio": st["estimate_max_ratio"], "inflight_peak": st["inflight_peak"],
-                          "higher_is_better": False, "n_gpus": ws,
-                          "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
-                          "gpu_launches": r["launches"], "sequential_fp64": r["sequential"],
-                          "config": r["config"]}))
+        obj = serving_object(r, args)
+        line = {"metric": "serving p50/p99 latency", "value": obj["p50_ms"], "unit": "ms", "higher_is_better": False,
+                "n_gpus": ws, "data": "synthetic"}
+        line.update(obj)
+        print(json.dumps(line))
     return 0
 
 

@@ -61,7 +61,7 @@ typedef enum {
 enum { NN_MEM_HOST = 0, NN_MEM_DEVICE = 1 };
 enum { NN_COEF_TENSOR = 0, NN_COEF_VELOCITY = 1 };
 enum { NN_SOLVER_GPCG = 0, NN_SOLVER_LBFGS = 1, NN_SOLVER_TRON = 2 };
-enum { NN_PREC_FP64 = 0, NN_PREC_MIXED = 1 };
+enum { NN_PREC_FP64 = 0, NN_PREC_MIXED = 1, NN_PREC_AUTO = 2 };
 enum { NN_FMT_SELL = 0, NN_FMT_CSR = 1 };
 
 /* Last error message of the calling thread ("" if none). */
@@ -180,7 +180,11 @@ typedef struct {
                             NN_SOLVER_TRON (trust-region Newton for bounds, Lin & More 1999;
                             Sec. 3.1 and 5.1); L-BFGS and TRON run in FP64 on the SELL format */
     int precision;       /* NN_PREC_FP64, or NN_PREC_MIXED: FP32 values/vectors in inner solves,
-                            FP64 residual, refinement and KKT */
+                            FP64 residual, refinement and KKT, or NN_PREC_AUTO: MIXED for systems
+                            whose FP32 operator exceeds 48 MB (it streams from HBM every product,
+                            and FP32 values cut those bytes by a third) when the system has the
+                            FP32 copy, FP64 otherwise (smaller solves are latency-bound and gain
+                            nothing from FP32); batched solves take AUTO as FP64 */
     int format;          /* NN_FMT_SELL or NN_FMT_CSR (FP64 only) */
     double rtol;         /* stop when kkt_rel <= rtol (default 1e-10) */
     int64_t max_iter;    /* cap on matrix-vector products (default 200000) */
@@ -366,6 +370,8 @@ typedef struct {
     size_t bytes_reserved_peak;      /* largest sum of admission estimates (never above budget) */
     int64_t estimate_overruns;       /* finished requests whose measured bytes exceeded the estimate */
     double estimate_max_ratio;       /* largest measured / estimated bytes of a finished request */
+    int64_t queued;                  /* requests waiting for admission now */
+    int64_t inflight;                /* requests admitted and not finished now */
 } nn_serve_stats_t;
 
 void nn_serve_opts_default(nn_serve_opts *o);

@@ -35,7 +35,7 @@ STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "INFEASIBLE", 3: "NOT_SPD", 4: "OO
 NN_MEM_HOST, NN_MEM_DEVICE = 0, 1
 NN_COEF_TENSOR, NN_COEF_VELOCITY = 0, 1
 NN_SOLVER_GPCG, NN_SOLVER_LBFGS, NN_SOLVER_TRON = 0, 1, 2
-NN_PREC_FP64, NN_PREC_MIXED = 0, 1
+NN_PREC_FP64, NN_PREC_MIXED, NN_PREC_AUTO = 0, 1, 2
 NN_FMT_SELL, NN_FMT_CSR = 0, 1
 
 COPY = dict(K_rowptr=0, K_col=1, K_val=2, M_val=3, F=4, free_node=5, A_rowptr=6, A_col=7, A_val=8, b0=9,
@@ -93,7 +93,7 @@ class nn_serve_stats_t(ctypes.Structure):
                 ("p50_ms", c_double), ("p99_ms", c_double), ("mean_ms", c_double), ("solves_per_s", c_double),
                 ("bytes_resident", c_size_t), ("bytes_peak", c_size_t), ("budget", c_size_t),
                 ("inflight_peak", c_int64), ("bytes_reserved_peak", c_size_t), ("estimate_overruns", c_int64),
-                ("estimate_max_ratio", c_double)]
+                ("estimate_max_ratio", c_double), ("queued", c_int64), ("inflight", c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -84,7 +84,7 @@ nn_status check_opts(const nn_solve_opts *o) {
         set_error("unknown solver %d", o->solver);
         return NN_ERR_INVALID_ARG;
     }
-    if (o->precision != NN_PREC_FP64 && o->precision != NN_PREC_MIXED) {
+    if (o->precision != NN_PREC_FP64 && o->precision != NN_PREC_MIXED && o->precision != NN_PREC_AUTO) {
         set_error("unknown precision %d", o->precision);
         return NN_ERR_INVALID_ARG;
     }

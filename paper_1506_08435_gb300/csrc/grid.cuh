@@ -66,6 +66,7 @@ struct GridArgs {
     double *xprev2;         // [n] c^(n-2) (quadratic extrapolation)
     uint8_t *fmask;         // [n] face mask of the CG phases
     int tma_slot_entries;   // FMT 3: 32 x the widest slice (slot size of the streamed operator)
+    int tma_slots;          // FMT 3: slots per warp
 };
 
 // Initial iterate of a backward-Euler step: linear extrapolation of the last
@@ -165,6 +166,7 @@ __global__ void __launch_bounds__(TPB, TPB >= 512 ? 1 : mode_min_blocks(MODE)) k
         A32tma.val = a.A32.val;
         A32tma.rsum = a.A32.rsum;
         A32tma.slot_entries = a.tma_slot_entries;
+        A32tma.D = a.tma_slots;
         A32tma.error = &a.bar->error;
         A32tma.setup(op_smem);
     }

@@ -223,7 +223,8 @@ using SellF32DiffLocal = SellF32DiffX<true>;
 // the grid's error word (the host then reports NN_ERR_TIMEOUT), waits for
 // the warp's other copies in flight and skips the rest of the product.
 struct SellF32DiffTma {
-    static constexpr int D = 2;           // slots per warp
+    static constexpr int kMaxSlots = 4;   // most slots per warp
+    int D;                                // slots per warp (2..kMaxSlots)
     int64_t n, nslices;
     const int64_t *__restrict__ sptr;
     const int32_t *__restrict__ col;
@@ -235,11 +236,12 @@ struct SellF32DiffTma {
     unsigned char *buf;                   // [warps][D][slot_entries * 8] (shared memory)
     int *error;                           // grid error word (global memory)
 
-    // Shared memory a block of `warps` warps needs: mbarriers (512 B) and
-    // use counters (128 B) in a 1 KB header, then the slots.
-    static constexpr int kHeader = 1024;
-    __host__ __device__ static size_t smem_bytes(int warps, int slot_entries) {
-        return kHeader + (size_t)warps * D * slot_entries * 8;
+    // Shared memory a block of `warps` warps with `slots` slots each needs:
+    // mbarriers (at most 32 x 4 x 8 B) and use counters (128 B) in a 2 KB
+    // header, then the slots.
+    static constexpr int kHeader = 2048;
+    __host__ __device__ static size_t smem_bytes(int warps, int slots, int slot_entries) {
+        return kHeader + (size_t)warps * slots * slot_entries * 8;
     }
 
     // Carves the block's shared memory and initialises its mbarriers
@@ -247,7 +249,7 @@ struct SellF32DiffTma {
     __device__ void setup(unsigned char *smem) {
         const int nw = blockDim.x >> 5;
         bars = reinterpret_cast<uint64_t *>(smem);
-        uses = reinterpret_cast<unsigned *>(smem + 8 * kMaxWarps * D);
+        uses = reinterpret_cast<unsigned *>(smem + 8 * kMaxWarps * kMaxSlots);
         buf = smem + kHeader;
         if (threadIdx.x < (unsigned)(nw * D)) mbar_init(bars + threadIdx.x, 1);
         if (threadIdx.x < (unsigned)nw) uses[threadIdx.x] = 0;

@@ -17,11 +17,17 @@
 
 namespace nnqp {
 
-// Products allowed to one FP32 inner solve: CG needs O(sqrt(cond)) steps
-// and cond grows like n^(2/d); 8 sqrt(n) (at least 4000) is ample where FP32
-// converges at all.
+// Products allowed to the first FP32 inner solve.  It starts from zero and
+// has to do most of the solve's work: CG needs O(sqrt(cond)) steps and cond
+// grows like n^(2/d), and GPCG adds the phases that find the active set
+// (steady solves of 5e4 - 1e6 unknowns from zero take 6k - 40k products).  A
+// cap only guards against an FP32 solve that cannot converge, so it is set
+// well above that: 64 sqrt(n), at least 4000.  Every later inner solve (a
+// correction of a residual already reduced) may take at most twice the
+// products of the first, so a stagnating FP32 solve is cut off early and
+// the contraction test then hands the solve to FP64.
 __host__ __device__ __forceinline__ int64_t inner_product_cap(int64_t n) {
-    const int64_t c = (int64_t)(8.0 * sqrt((double)n));
+    const int64_t c = (int64_t)(64.0 * sqrt((double)n));
     return c > 4000 ? c : 4000;
 }
 
@@ -131,7 +137,15 @@ __device__ int mixed_solve(Team &T, const Rows &R, const Op64 &A, const Op32 &A3
         if (c.max_spmv > inner_cap) c.max_spmv = inner_cap;
         GpcgStats is;
         Bounds<float> B{0.0, 0.0, l32, h32};
-        int s = gpcg_call<SPLIT, Team, Op32, float, CGV>(T, R, A32, B, v, c, is);
+        // the FP32 inner solve never takes the pipelined CG form: its extra
+        // recurrences lose accuracy in FP32 (the inner solves of steady
+        // 1e5 - 1e6 unknown problems stalled at 10x the FP64 product count);
+        // the Chronopoulos-Gear form has the same single fused reduction
+        int s = gpcg_call<SPLIT, Team, Op32, float, (CGV == 2 ? 1 : CGV)>(T, R, A32, B, v, c, is);
+        if (ref == 0) {
+            const int64_t later = 2 * (is.spmv > 1000 ? is.spmv : 1000);
+            if (later < inner_cap) inner_cap = later;
+        }
         st.spmv32 += is.spmv;
         st.cg += is.cg;
         st.phases += is.phases;

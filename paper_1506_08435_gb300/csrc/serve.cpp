@@ -105,6 +105,15 @@ size_t estimate_bytes(int dim, int64_t N, int64_t E, bool mixed) {
     return (size_t)b;
 }
 
+// Whether a request needs the FP32 operator copy: mixed precision, or
+// NN_PREC_AUTO on a system whose FP32 operator (about 16 or 7.5 nonzeros per
+// node in 3D or 2D, 8 bytes each) exceeds the 48 MB streaming threshold.
+bool uses_fp32(const nn_solve_opts &o, int dim, int64_t N) {
+    if (o.precision == NN_PREC_MIXED) return true;
+    const double nnz = (dim == 3 ? 16.0 : 7.5) * (double)N;
+    return o.precision == NN_PREC_AUTO && nnz * 8.0 > 48.0 * (1 << 20);
+}
+
 void worker_loop(Server *sv) {
     cudaSetDevice(sv->device);
     cudaStream_t st;
@@ -121,7 +130,7 @@ void worker_loop(Server *sv) {
         }
         nn_assemble_opts ao;
         nn_assemble_opts_default(&ao);
-        ao.build_mixed = r->opts.precision == NN_PREC_MIXED;
+        ao.build_mixed = uses_fp32(r->opts, r->p.dim, r->N);
         nn_system *s = nullptr;
         nn_status stt = assemble_impl(&r->p, &ao, st, &s);
         double *dc = nullptr;
@@ -301,7 +310,7 @@ nn_status nn_serve_submit(nn_server *h, const nn_problem *p, const nn_solve_opts
         set_error("nn_serve_submit: empty mesh");
         return NN_ERR_INVALID_ARG;
     }
-    r->bytes = estimate_bytes(dim, r->N, r->E, r->opts.precision == NN_PREC_MIXED);
+    r->bytes = estimate_bytes(dim, r->N, r->E, uses_fp32(r->opts, dim, r->N));
     if (r->bytes > sv->budget) {
         set_error("nn_serve_submit: the request alone (%zu bytes) exceeds the budget", r->bytes);
         return NN_ERR_INVALID_ARG;
@@ -425,6 +434,8 @@ nn_status nn_serve_stats(nn_server *h, nn_serve_stats_t *st) {
     st->bytes_reserved_peak = sv->reserved_peak;
     st->estimate_overruns = sv->overruns;
     st->estimate_max_ratio = sv->worst_ratio;
+    st->queued = (int64_t)sv->queue.size();
+    st->inflight = sv->inflight;
     if (!sv->lat_ms.empty()) {
         std::vector<double> v = sv->lat_ms;
         std::sort(v.begin(), v.end());

@@ -181,9 +181,10 @@ constexpr double kStreamBytes = 48.0 * (1 << 20);
 // Most shared memory a block's staged operator slices may take.
 constexpr size_t kSmemOperatorBytes = 192 * 1024;
 // Shared-memory budget of the streamed FP32 operator's slots per block
-// (8 warps x 2 slots x 32 rows x 16 entries x 8 bytes, plus a 1 KB header).
+// (8 warps x 2 slots x 32 rows x 16 entries x 8 bytes, plus a 2 KB header).
 constexpr size_t kTmaSmemBytes = 66 * 1024;
-// The same for one 768-thread block per SM (24 warps).
+// The same for one 512-thread block per SM (16 warps x 3 slots of 14-wide
+// slices fit).
 constexpr size_t kTmaSmemBytesLarge = 196 * 1024;
 // Threads per block of the large-system grids (one block per SM): FP64,
 // and mixed precision.
@@ -367,6 +368,8 @@ nn_status plan_build(nn_system *s, const nn_solve_opts *o, int mode, int nsteps,
     a.ctl.cg_bound_stop = 0;
     if (const char *e = getenv("NNQP_CG_VARIANT")) a.ctl.cg_variant = atoi(e);
     if (const char *e = getenv("NNQP_CG_BOUND_STOP")) a.ctl.cg_bound_stop = atoi(e);
+    a.ctl.chunk_pf = 0;
+    if (const char *e = getenv("NNQP_CHUNK_PF")) a.ctl.chunk_pf = atoi(e);
     if (const char *e = getenv("NNQP_GP_MAX")) a.ctl.gp_max = atoi(e);
     if (const char *e = getenv("NNQP_ETA1")) a.ctl.eta1 = atof(e);
     if (const char *e = getenv("NNQP_ETA2")) a.ctl.eta2 = atof(e);
@@ -496,9 +499,14 @@ nn_status plan_build(nn_system *s, const nn_solve_opts *o, int mode, int nsteps,
         for (int64_t k = 0; k < slices; ++k)
             wmax = std::max<int64_t>(wmax, (s->sptr_host[(size_t)k + 1] - s->sptr_host[(size_t)k]) >> 5);
         const int se = (int)(32 * std::max<int64_t>(wmax, 2));
-        const size_t bytes = SellF32DiffTma::smem_bytes(tpb / 32, se);
-        GridKernel kt = grid_kernel(mode, FMT_SELL_TMA, 0, tpb);
         const size_t budget = tpb == kLargeThreadsMixed ? kTmaSmemBytesLarge : kTmaSmemBytes;
+        // as many slots per warp as the budget holds (2 .. 4): D - 1 slices
+        // of every warp in flight
+        int slots = SellF32DiffTma::kMaxSlots;
+        while (slots > 2 && SellF32DiffTma::smem_bytes(tpb / 32, slots, se) > budget) --slots;
+        if (const char *e = getenv("NNQP_TMA_SLOTS")) slots = std::min(std::max(atoi(e), 2), SellF32DiffTma::kMaxSlots);
+        const size_t bytes = SellF32DiffTma::smem_bytes(tpb / 32, slots, se);
+        GridKernel kt = grid_kernel(mode, FMT_SELL_TMA, 0, tpb);
         if (kt && bytes <= budget &&
             cudaFuncSetAttribute((const void *)kt, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)budget) ==
                 cudaSuccess) {
@@ -511,6 +519,7 @@ nn_status plan_build(nn_system *s, const nn_solve_opts *o, int mode, int nsteps,
                 maxg = per * sms;
                 want = full_grid ? maxg : std::min(want, maxg);
                 a.tma_slot_entries = se;
+                a.tma_slots = slots;
             }
         }
         cudaGetLastError();   // a refused attribute leaves the load-based kernel in use
@@ -782,9 +791,13 @@ nn_status solve_entry(nn_system *s, const nn_solve_opts *o, int mode, int nsteps
     return r;
 }
 
+// NN_PREC_AUTO: mixed precision where the FP32 operator streams from HBM.
+bool auto_mixed(const nn_system *s) { return s->has_mixed && (double)s->nnzF * 8.0 > kStreamBytes; }
+
 int mode_for(const nn_system *s, const nn_solve_opts *o) {
-    if (s->dt > 0.0) return o->precision == NN_PREC_MIXED ? MODE_MIXED_TR : MODE_TRANSIENT;
-    return o->precision == NN_PREC_MIXED ? MODE_MIXED : MODE_STEADY;
+    const bool mixed = o->precision == NN_PREC_MIXED || (o->precision == NN_PREC_AUTO && auto_mixed(s));
+    if (s->dt > 0.0) return mixed ? MODE_MIXED_TR : MODE_TRANSIENT;
+    return mixed ? MODE_MIXED : MODE_STEADY;
 }
 
 // Co-resident 256-thread blocks per SM of the steady/mixed solve kernels

@@ -444,3 +444,22 @@ def test_serving_per_request_options_and_measured_bytes_within_the_estimate():
         P.nn_serve_submit(sv, P.Problem(pick[0]), P.solve_opts(solver=P.NN_SOLVER_LBFGS))
     assert e.value.status == P.NN_ERR_INVALID_ARG
     P.nn_serve_destroy(sv)
+
+
+def test_auto_precision_picks_fp32_only_for_streaming_operators():
+    """NN_PREC_AUTO solves a system whose FP32 operator exceeds the 48 MB
+    streaming threshold in mixed precision (refinements in FP64) and a
+    smaller one in plain FP64; both meet the oracle's KKT test."""
+    for n, mixed in ((20, False), (76, True)):
+        spec = I.config3_steady_3d(n=n, seed=3)
+        s = gpu_system(spec, build_mixed=1)
+        d = s.describe()
+        assert (d["nnz_free"] * 8 > 48 * 2 ** 20) == mixed
+        c = torch.zeros(spec.n_nodes, dtype=torch.float64, device=DEV)
+        info = P.nn_qp_solve(s, c, P.solve_opts(precision=P.NN_PREC_AUTO))
+        assert info["status"] == 0, info
+        assert (info["refinements"] > 0) == mixed, (n, info)
+        _, red = oracle_reduced(spec)
+        x = c.cpu().numpy()[red.free]
+        kk = O.kkt(red.A, red.rhs(), spec.lo, spec.hi, x)
+        assert kk["bounds_ok"] and kk["kkt_rel"] <= 1e-8, kk

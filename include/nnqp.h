@@ -323,6 +323,50 @@ nn_status nn_spmv(const nn_system *s, const double *x, double *y, int format, in
  *     allocating call.  Asynchronous. */
 nn_status nn_spmv_mixed_noalloc(const nn_system *s, const double *x, double *y, void *stream);
 
+/* ------------------------------------------------------- row sharding
+ * One QP spread over several ranks (one GPU each), as the paper scales one
+ * problem by domain decomposition (PETSc/TAO over MPI, Sec. 3.1; strong
+ * scaling, Sec. 5.1.2): rank r owns a contiguous range of the free unknowns
+ * (a z-slab of the structured meshes, ranges balanced by nonzeros); a
+ * product first gathers the ghost values its rows reference from their
+ * owners, and a dot product is a local sum plus an all-reduce.  The plan is
+ * computed on the host from the CSR pattern of A (nn_system_copy_out arrays
+ * 6 and 7, or any CSR pattern with sorted columns), so every rank can build
+ * its own and the plans agree.  The exchange itself belongs to the caller's
+ * communicator (NCCL, MPI, ...); nn_shard_spmv is the local product. */
+typedef struct {
+    int rank, nranks;
+    int64_t n;                      /* free unknowns of the whole system */
+    int64_t row0, row1;             /* owned rows [row0, row1) */
+    int64_t n_halo;                 /* ghosts: columns of owned rows outside [row0, row1) */
+    int64_t nnz;                    /* nonzeros of the owned rows */
+    int64_t n_send;                 /* (destination, owned id) pairs other ranks need as ghosts */
+} nn_shard_desc;
+
+/* Sizes of rank `rank`'s shard of the n x n pattern (host arrays rowptr
+ * int64 [n+1], col int32 [nnz]).  Errors: INVALID_ARG. */
+nn_status nn_shard_plan(int64_t n, const int64_t *rowptr, const int32_t *col, int nranks, int rank,
+                        nn_shard_desc *d);
+
+/* Fills caller host arrays of the shard (sizes from nn_shard_plan):
+ *   local_rowptr int64 [row1 - row0 + 1], local_col int32 [nnz]: the owned
+ *     rows with column c renumbered c - row0 if owned, else
+ *     (row1 - row0) + h where h is its index in halo_ids;
+ *   halo_ids int64 [n_halo] (ascending global ids), halo_owner int32 [n_halo];
+ *   send_ids int64 [n_send], send_rank int32 [n_send]: the owned ids each
+ *     other rank holds as ghosts, ordered by destination rank, then id.
+ * The values of the local rows are A's values of rows row0..row1-1 in their
+ * stored order.  Errors: INVALID_ARG. */
+nn_status nn_shard_build(int64_t n, const int64_t *rowptr, const int32_t *col, int nranks, int rank,
+                         int64_t *local_rowptr, int32_t *local_col, int64_t *halo_ids, int32_t *halo_owner,
+                         int64_t *send_ids, int32_t *send_rank);
+
+/* y = A_local x_ext on the device: local_rowptr/local_col/val of a shard
+ * (device copies), x_ext [nrows + n_halo] = owned entries then ghosts, y
+ * [nrows].  FP64.  Stream-ordered, asynchronous.  Errors: INVALID_ARG, CUDA. */
+nn_status nn_shard_spmv(int64_t nrows, const int64_t *local_rowptr, const int32_t *local_col, const double *val,
+                        const double *x_ext, double *y, void *stream);
+
 /* --------------------------------------------------------------- batching */
 
 /* Solves `count` independent steady systems in ONE persistent launch.

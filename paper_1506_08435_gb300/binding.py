@@ -88,6 +88,11 @@ class nn_serve_opts(ctypes.Structure):
                 ("solve", nn_solve_opts)]
 
 
+class nn_shard_desc(ctypes.Structure):
+    _fields_ = [("rank", c_int), ("nranks", c_int), ("n", c_int64), ("row0", c_int64), ("row1", c_int64),
+                ("n_halo", c_int64), ("nnz", c_int64), ("n_send", c_int64)]
+
+
 class nn_serve_stats_t(ctypes.Structure):
     _fields_ = [("submitted", c_int64), ("completed", c_int64), ("failed", c_int64), ("rejected", c_int64),
                 ("p50_ms", c_double), ("p99_ms", c_double), ("mean_ms", c_double), ("solves_per_s", c_double),
@@ -105,7 +110,8 @@ EXPORTS = ["nn_last_error", "nn_version", "nn_kernel_launches", "nn_device_alloc
            "nn_spmv_mixed_noalloc",
            "nn_batch_solve", "nn_batch_autotune", "nn_serve_opts_default", "nn_serve_create",
            "nn_serve_submit", "nn_serve_poll", "nn_serve_drain", "nn_serve_stats", "nn_serve_destroy",
-           "nn_plan_create", "nn_plan_launch", "nn_plan_result", "nn_plan_destroy"]
+           "nn_plan_create", "nn_plan_launch", "nn_plan_result", "nn_plan_destroy",
+           "nn_shard_plan", "nn_shard_build", "nn_shard_spmv"]
 
 _lib = None
 
@@ -160,6 +166,9 @@ def lib():
     L.nn_serve_stats.argtypes = [vp, POINTER(nn_serve_stats_t)]
     L.nn_serve_destroy.argtypes = [vp]
     L.nn_serve_destroy.restype = None
+    L.nn_shard_plan.argtypes = [c_int64, vp, vp, c_int, c_int, POINTER(nn_shard_desc)]
+    L.nn_shard_build.argtypes = [c_int64, vp, vp, c_int, c_int, vp, vp, vp, vp, vp, vp]
+    L.nn_shard_spmv.argtypes = [c_int64, vp, vp, vp, vp, vp, vp]
     _lib = L
     return L
 
@@ -492,3 +501,41 @@ def nn_serve_destroy(server):
     if server.handle is not None and server.handle.value:
         lib().nn_serve_destroy(server.handle)
         server.handle = None
+
+
+# ---------------------------------------------------------------- row sharding
+
+def nn_shard_plan(rowptr, col, nranks, rank):
+    """Shard sizes of rank `rank` for the CSR pattern (numpy int64 rowptr,
+    int32 col, host)."""
+    rowptr = np.ascontiguousarray(rowptr, np.int64)
+    col = np.ascontiguousarray(col, np.int32)
+    d = nn_shard_desc()
+    _check(lib().nn_shard_plan(len(rowptr) - 1, rowptr.ctypes.data, col.ctypes.data, nranks, rank, byref(d)))
+    return {k: getattr(d, k) for k, _ in d._fields_}
+
+
+def nn_shard_build(rowptr, col, nranks, rank):
+    """The shard's local CSR pattern, ghosts and send list (numpy arrays)."""
+    rowptr = np.ascontiguousarray(rowptr, np.int64)
+    col = np.ascontiguousarray(col, np.int32)
+    d = nn_shard_plan(rowptr, col, nranks, rank)
+    nrows = d["row1"] - d["row0"]
+    out = dict(local_rowptr=np.zeros(nrows + 1, np.int64), local_col=np.zeros(max(d["nnz"], 1), np.int32),
+               halo_ids=np.zeros(max(d["n_halo"], 1), np.int64), halo_owner=np.zeros(max(d["n_halo"], 1), np.int32),
+               send_ids=np.zeros(max(d["n_send"], 1), np.int64), send_rank=np.zeros(max(d["n_send"], 1), np.int32))
+    _check(lib().nn_shard_build(len(rowptr) - 1, rowptr.ctypes.data, col.ctypes.data, nranks, rank,
+                                *[out[k].ctypes.data for k in ("local_rowptr", "local_col", "halo_ids", "halo_owner",
+                                                               "send_ids", "send_rank")]))
+    out["local_col"] = out["local_col"][:d["nnz"]]
+    for k, m in (("halo_ids", "n_halo"), ("halo_owner", "n_halo"), ("send_ids", "n_send"), ("send_rank", "n_send")):
+        out[k] = out[k][:d[m]]
+    out.update(d)
+    return out
+
+
+def nn_shard_spmv(nrows, local_rowptr, local_col, val, x_ext, y, stream=None):
+    """y = A_local x_ext on the device (torch tensors on the GPU)."""
+    _check(lib().nn_shard_spmv(nrows, _ptr(local_rowptr)[0], _ptr(local_col)[0], _ptr(val)[0], _ptr(x_ext)[0],
+                               _ptr(y)[0], _stream(stream)))
+    return y

@@ -73,6 +73,8 @@ nn_status kkt_impl(const nn_system *s, const double *c, const double *c_prev, in
                    cudaStream_t st);
 nn_status spmv_impl(const nn_system *s, const double *x, double *y, int format, int precision, cudaStream_t st);
 nn_status spmv_mixed_noalloc_impl(const nn_system *s, const double *x, double *y, cudaStream_t st);
+nn_status csr_spmv_impl(int64_t nrows, const int64_t *rowptr, const int32_t *col, const double *val,
+                        const double *x, double *y, cudaStream_t st);
 nn_status check_opts(const nn_solve_opts *o);
 
 nn_status check_opts(const nn_solve_opts *o) {
@@ -303,6 +305,16 @@ nn_status nn_spmv(const nn_system *s, const double *x, double *y, int format, in
         return NN_ERR_INVALID_ARG;
     }
     return spmv_impl(s, x, y, format, precision, S(stream));
+}
+
+nn_status nn_shard_spmv(int64_t nrows, const int64_t *local_rowptr, const int32_t *local_col, const double *val,
+                        const double *x_ext, double *y, void *stream) {
+    clear_error();
+    if (nrows < 0 || (nrows > 0 && (!local_rowptr || !local_col || !val || !x_ext || !y))) {
+        set_error("nn_shard_spmv: nrows >= 0 and device arrays are required");
+        return NN_ERR_INVALID_ARG;
+    }
+    return csr_spmv_impl(nrows, local_rowptr, local_col, val, x_ext, y, S(stream));
 }
 
 nn_status nn_spmv_mixed_noalloc(const nn_system *s, const double *x, double *y, void *stream) {

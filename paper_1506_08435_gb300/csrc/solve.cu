@@ -707,6 +707,19 @@ nn_status spmv_impl(const nn_system *s, const double *x, double *y, int format, 
     return NN_OK;
 }
 
+// y = A_local x_ext for one shard of a row-sharded system: CSR rows with
+// local column ids (device arrays; x_ext holds the owned entries followed by
+// the ghosts).
+nn_status csr_spmv_impl(int64_t nrows, const int64_t *rowptr, const int32_t *col, const double *val,
+                        const double *x, double *y, cudaStream_t st) {
+    if (nrows == 0) return NN_OK;
+    const int64_t slices = (nrows + 31) / 32;
+    const int nb = (int)std::max<int64_t>((slices + 7) / 8, 1);
+    (k_spmvcsr<<<nb, 256, 0, st>>>(CsrF64{nrows, slices, rowptr, col, val}, x, y), count_launch());
+    NN_CUDA_TRY(cudaGetLastError());
+    return NN_OK;
+}
+
 // ------------------------------------------------------------------ no-allocation product
 //
 // nn_spmv_mixed_noalloc computes the same FP32-value product as nn_spmv with

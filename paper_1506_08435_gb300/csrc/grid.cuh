@@ -23,6 +23,15 @@ __host__ __device__ constexpr bool mode_mixed(int m) { return m == MODE_MIXED ||
 // Blocks per SM the kernel is compiled for: the transient drivers run one
 // block per SM on mid-size systems and get the larger register budget.
 __host__ __device__ constexpr int mode_min_blocks(int m) { return mode_transient(m) ? 2 : 3; }
+// CG form of the FP32 inner solves of a mixed mode whose FP64 form is cgv:
+// steady solves from zero do not take the pipelined form (its recurrences
+// drift in FP32 over thousands of iterations: the inner solves of 1e5 - 1e6
+// unknown steady problems stalled at ~10x the FP64 product count) but the
+// Chronopoulos-Gear form, with the same single fused reduction; the short,
+// warm-started inner solves of backward-Euler steps keep the pipelined one.
+__host__ __device__ constexpr int inner_cg_form(int mode, int cgv) {
+    return (mode == MODE_MIXED && cgv == 2) ? 1 : cgv;
+}
 
 struct GridArgs {
     int mode;
@@ -210,15 +219,15 @@ __global__ void __launch_bounds__(TPB, TPB >= 512 ? 1 : mode_min_blocks(MODE)) k
                                  a.v64[6], a.v64[7], a.v64[8], b, a.dinv64, a.fmask, a.v64[10]};
             MixedStats ms;
             if constexpr (FMT == 2)
-                status = mixed_solve<CGV, true>(T, R, a.A, A32loc, a.lo, a.hi, b, x, v, a.v32[9], a.v32[10],
+                status = mixed_solve<CGV, inner_cg_form(MODE, CGV), true>(T, R, a.A, A32loc, a.lo, a.hi, b, x, v, a.v32[9], a.v32[10],
                                                  a.v32[11], v64, a.rtol * den, a.inner_rtol, a.max_ref,
                                                  a.ctl.max_spmv, a.inner_cap, a.ctl, a.ctl, ms);
             else if constexpr (FMT == 3)
-                status = mixed_solve<CGV, (TPB < 512)>(T, R, a.A, A32tma, a.lo, a.hi, b, x, v, a.v32[9], a.v32[10],
+                status = mixed_solve<CGV, inner_cg_form(MODE, CGV), (TPB < 512)>(T, R, a.A, A32tma, a.lo, a.hi, b, x, v, a.v32[9], a.v32[10],
                                                  a.v32[11], v64, a.rtol * den, a.inner_rtol, a.max_ref,
                                                  a.ctl.max_spmv, a.inner_cap, a.ctl, a.ctl, ms);
             else
-                status = mixed_solve<CGV, true>(T, R, a.A, a.A32, a.lo, a.hi, b, x, v, a.v32[9], a.v32[10],
+                status = mixed_solve<CGV, inner_cg_form(MODE, CGV), true>(T, R, a.A, a.A32, a.lo, a.hi, b, x, v, a.v32[9], a.v32[10],
                                                  a.v32[11], v64, a.rtol * den, a.inner_rtol, a.max_ref,
                                                  a.ctl.max_spmv, a.inner_cap, a.ctl, a.ctl, ms);
             if (status == ST_TIMEOUT) return;

@@ -71,7 +71,8 @@ __device__ __forceinline__ int gpcg_call(Team &T, const Rows &R, const Op &A, co
         return gpcg_solve<Team, Op, V, CGV>(T, R, A, B, v, C, st);
 }
 
-template <int CGV, bool SPLIT, class Team, class Op64, class Op32>
+// CGV: CG form of the FP64 fallback; CGV32: of the FP32 inner solves.
+template <int CGV, int CGV32, bool SPLIT, class Team, class Op64, class Op32>
 __device__ int mixed_solve(Team &T, const Rows &R, const Op64 &A, const Op32 &A32, double lo, double hi,
                            const double *b, double *x, GpcgVecs<float> &v, float *r32, float *l32, float *h32,
                            GpcgVecs<double> &v64, double tol, double inner_rtol, int max_ref, int64_t max_spmv,
@@ -137,11 +138,7 @@ __device__ int mixed_solve(Team &T, const Rows &R, const Op64 &A, const Op32 &A3
         if (c.max_spmv > inner_cap) c.max_spmv = inner_cap;
         GpcgStats is;
         Bounds<float> B{0.0, 0.0, l32, h32};
-        // the FP32 inner solve never takes the pipelined CG form: its extra
-        // recurrences lose accuracy in FP32 (the inner solves of steady
-        // 1e5 - 1e6 unknown problems stalled at 10x the FP64 product count);
-        // the Chronopoulos-Gear form has the same single fused reduction
-        int s = gpcg_call<SPLIT, Team, Op32, float, (CGV == 2 ? 1 : CGV)>(T, R, A32, B, v, c, is);
+        int s = gpcg_call<SPLIT, Team, Op32, float, CGV32>(T, R, A32, B, v, c, is);
         if (ref == 0) {
             const int64_t later = 2 * (is.spmv > 1000 ? is.spmv : 1000);
             if (later < inner_cap) inner_cap = later;

@@ -180,16 +180,14 @@ namespace {
 constexpr double kStreamBytes = 48.0 * (1 << 20);
 // Most shared memory a block's staged operator slices may take.
 constexpr size_t kSmemOperatorBytes = 192 * 1024;
-// Shared-memory budget of the streamed FP32 operator's slots per block
-// (8 warps x 2 slots x 32 rows x 16 entries x 8 bytes, plus a 2 KB header).
-constexpr size_t kTmaSmemBytes = 66 * 1024;
-// The same for one 512-thread block per SM (16 warps x 3 slots of 14-wide
-// slices fit).
-constexpr size_t kTmaSmemBytesLarge = 196 * 1024;
-// Threads per block of the large-system grids (one block per SM): FP64,
-// and mixed precision.
+// Shared-memory budget of the streamed FP32 operator's slots per block: one
+// 768-thread block per SM, 24 warps x 2 slots of 32 rows x up to 16 entries
+// x 8 bytes, plus a 2 KB header.
+constexpr size_t kTmaSmemBytes = 196 * 1024;
+// Threads per block of the large-system grids (one block per SM), and of
+// the large mixed grid where the streamed operator does not apply.
 constexpr int kLargeThreads = 768;
-constexpr int kLargeThreadsMixed = 512;
+constexpr int kLargeThreadsLoads = 512;
 // Threads per block of the projected L-BFGS kernel (128 was measured too:
 // faster on the 50^2 problem, slower on the 40^3 transient run).
 constexpr int kLbfgsThreads = 256;
@@ -410,20 +408,28 @@ nn_status plan_build(nn_system *s, const nn_solve_opts *o, int mode, int nsteps,
     // Large systems (more than 32 slices per SM) run one 768-thread block
     // per SM with the textbook CG form: the warps of three 256-thread blocks,
     // a third of the barrier arrivals and reduction partials.  (Served
-    // requests of that size take the whole device, so they may too.)
+    // requests of that size take the whole device, so they may too.)  Mixed
+    // solves of that size take the 768-thread kernel with the streamed FP32
+    // operator (the only one built at that size; below, the 512-thread
+    // load-based kernel where the streamed operator does not apply).
     const bool large = !driver && (slices > (int64_t)4 * 8 * sms || force_large);
     if (!driver && slices <= (int64_t)4 * 8 * sms && slices > (int64_t)8 * sms / 2) tpb = 512;
     if (!driver && (force_tpb == 256 || force_tpb == 512)) tpb = force_tpb;
-    // Mixed solves of that size run 512-thread blocks (one per SM): their
-    // FP32 inner solve, inlined, needs the larger register budget.
-    if (large && a.ctl.cg_variant == 0 && fmt == NN_FMT_SELL && force_tpb != 512)
-        tpb = mixed ? kLargeThreadsMixed : kLargeThreads;
+    if (large && a.ctl.cg_variant == 0 && fmt == NN_FMT_SELL && force_tpb != 512) tpb = kLargeThreads;
     if (force_large) {
         a.A.stream = true;
         a.A32.stream = true;
     }
     if (const char *e = getenv("NNQP_GRID_THREADS")) tpb = atoi(e);
     GridKernel kern = lbfgs ? k_lbfgs_grid : tron ? k_tron_grid : grid_kernel(mode, fmt, a.ctl.cg_variant, tpb);
+    // a launch shape built only with the streamed FP32 operator: that kernel
+    // stands in for the sizing below and must be taken by the streaming
+    // choice further down (checked there)
+    bool tma_only = false;
+    if (!kern && !driver && mixed && fmt == NN_FMT_SELL && a.ctl.cg_variant == 0) {
+        kern = grid_kernel(mode, FMT_SELL_TMA, 0, tpb);
+        tma_only = kern != nullptr;
+    }
     if (!kern && !driver && tpb != kSolveThreads) {
         tpb = kSolveThreads;
         kern = grid_kernel(mode, fmt, a.ctl.cg_variant, tpb);
@@ -484,11 +490,11 @@ nn_status plan_build(nn_system *s, const nn_solve_opts *o, int mode, int nsteps,
     }
     // Large mixed solves stream the FP32 operator of their inner products
     // through shared memory with bulk asynchronous copies (FMT 3), when the
-    // slots of 8 warps fit the fixed budget and at least two blocks stay
-    // resident per SM.  NNQP_TMA_OP=0 keeps the load-based operator.
+    // slots of the block's 24 warps fit the budget.  NNQP_TMA_OP=0 keeps the
+    // load-based operator.
     const char *tma_env = getenv("NNQP_TMA_OP");
-    if (!driver && fmt == NN_FMT_SELL && mixed && (tpb == kSolveThreads || tpb == kLargeThreadsMixed) &&
-        a.ctl.cg_variant == 0 && a.A32.stream && dyn_smem == 0 && !(tma_env && tma_env[0] == '0')) {
+    if (!driver && fmt == NN_FMT_SELL && mixed && tpb == kLargeThreads && a.ctl.cg_variant == 0 && a.A32.stream &&
+        dyn_smem == 0 && !(tma_env && tma_env[0] == '0')) {
         if (s->sptr_host.empty()) {
             s->sptr_host.resize((size_t)slices + 1);
             NN_CUDA_TRY(cudaMemcpyAsync(s->sptr_host.data(), s->A64.sptr, sizeof(int64_t) * (slices + 1),
@@ -499,7 +505,7 @@ nn_status plan_build(nn_system *s, const nn_solve_opts *o, int mode, int nsteps,
         for (int64_t k = 0; k < slices; ++k)
             wmax = std::max<int64_t>(wmax, (s->sptr_host[(size_t)k + 1] - s->sptr_host[(size_t)k]) >> 5);
         const int se = (int)(32 * std::max<int64_t>(wmax, 2));
-        const size_t budget = tpb == kLargeThreadsMixed ? kTmaSmemBytesLarge : kTmaSmemBytes;
+        const size_t budget = kTmaSmemBytes;
         // as many slots per warp as the budget holds (2 .. 4): D - 1 slices
         // of every warp in flight
         int slots = SellF32DiffTma::kMaxSlots;
@@ -512,7 +518,7 @@ nn_status plan_build(nn_system *s, const nn_solve_opts *o, int mode, int nsteps,
                 cudaSuccess) {
             int per = 0;
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kt, tpb, bytes);
-            if (per * tpb >= 2 * kSolveThreads) {
+            if (per >= 1) {
                 const bool full_grid = want >= maxg;
                 kern = kt;
                 dyn_smem = bytes;
@@ -523,6 +529,18 @@ nn_status plan_build(nn_system *s, const nn_solve_opts *o, int mode, int nsteps,
             }
         }
         cudaGetLastError();   // a refused attribute leaves the load-based kernel in use
+    }
+    if (tma_only && dyn_smem == 0) {
+        // the streamed operator does not apply: the load-based kernel with
+        // 512-thread blocks, one per SM
+        tpb = kLargeThreadsLoads;
+        kern = grid_kernel(mode, fmt, a.ctl.cg_variant, tpb);
+        if (!kern) {
+            set_error("no solve kernel for this mode at %d threads per block", tpb);
+            return NN_ERR_INVALID_ARG;
+        }
+        maxg = max_coresident(kern, tpb);
+        want = large ? maxg : std::min(want, maxg);
     }
     // NNQP_TEST_STALL_BARRIER=1 makes the grid barrier wait for one block
     // that does not exist, so every wait runs into its time limit: the test of

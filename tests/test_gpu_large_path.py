@@ -1,10 +1,11 @@
 """Element-wise parity of the large-system solve path with the FP64 oracle.
 
 Systems above about 32 slices of 32 rows per SM (the 150^3 steady problem
-has 106,704 slices) run differently from mid-size ones: the operator streams
-through L2 with evict-first loads and slice prefetches, the CG phase is the
-textbook form, and the grid is the full co-resident grid of 256-thread
-blocks.  At full size that path can be checked only through the oracle's KKT
+has 106,704 slices) run differently from mid-size ones: one 768-thread block
+per SM, the textbook CG form with packed update passes, the FP64 operator
+streaming through L2 with evict-first loads and slice prefetches, and the
+FP32 operator of mixed inner solves streaming through shared memory by bulk
+asynchronous copies.  At full size that path can be checked only through the oracle's KKT
 test (the oracle needs hours for a 3.4M-unknown QP).  NNQP_FORCE_LARGE=1
 runs a system of any size through exactly that path, so here it is compared
 entry by entry with the oracle's minimiser at sizes the oracle solves in

@@ -61,7 +61,7 @@ __device__ void solve_instance(Team &T, const Rows &R, const BatchInst &I, int i
                              w6 + 7 * n, w6 + 8 * n, I.b0, I.dinv64, I.fm, w6 + 10 * n};
         MixedStats ms;
         status = mixed_solve<CGV, CGV, true>(T, R, A, A32, I.lo, I.hi, I.b0, x, v, w + 9 * n, w + 10 * n, w + 11 * n, v64,
-                                rtol * I.den, inner_rtol, max_ref, ctl.max_spmv, inner_product_cap(n), ctl, ctl, ms);
+                                rtol * I.den, inner_rtol, max_ref, ctl.max_spmv, batch_inner_product_cap(n), ctl, ctl, ms);
         cnt[1] = ms.spmv64;
         cnt[2] = ms.spmv32;
         cnt[3] = ms.cg;

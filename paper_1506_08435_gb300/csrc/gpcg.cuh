@@ -220,7 +220,6 @@ struct GpcgCtl {
                          // 1: Chronopoulos-Gear PCG (2 barriers, one fused reduction);
                          // 2: pipelined PCG (1 barrier: product, updates and
                          //    reduction in one pass; needs GpcgVecs::m2)
-    int chunk_pf;        // packed passes: L2 prefetch distance in iterations (0 = none)
     int cg_bound_stop;   // 1: end the CG phase as soon as x + s leaves the box;
                          // 0: run CG to its stall test, the projected search clips
 };
@@ -587,7 +586,7 @@ __device__ int gpcg_solve(Team &T, const Rows &R, const Op &A, const Bounds<V> &
                     const void *al6[6] = {v.s, v.p, v.r, v.q, v.dinv, v.z};
                     if (!count_cross && aligned16(al6)) {
                         constexpr int W = Pack<V>::W;
-                        R.each_chunk_pf<W>(pf5, (int)sizeof(V), C.chunk_pf, [&](int64_t i, int cnt) {
+                        R.each_chunk<W>([&](int64_t i, int cnt) {
                             if (cnt < W) {
                                 for (int j = 0; j < cnt; ++j) upd(i + j);
                                 return;
@@ -636,7 +635,7 @@ __device__ int gpcg_solve(Team &T, const Rows &R, const Op &A, const Bounds<V> &
                     const void *pf2[2] = {v.z, v.p};
                     if (aligned16(pf2)) {
                         constexpr int W = Pack<V>::W;
-                        R.each_chunk_pf<W>(pf2, (int)sizeof(V), C.chunk_pf, [&](int64_t i, int cnt) {
+                        R.each_chunk<W>([&](int64_t i, int cnt) {
                             if (cnt < W) {
                                 for (int j = 0; j < cnt; ++j) v.p[i + j] = v.z[i + j] + vb * v.p[i + j];
                                 return;

@@ -366,8 +366,6 @@ nn_status plan_build(nn_system *s, const nn_solve_opts *o, int mode, int nsteps,
     a.ctl.cg_bound_stop = 0;
     if (const char *e = getenv("NNQP_CG_VARIANT")) a.ctl.cg_variant = atoi(e);
     if (const char *e = getenv("NNQP_CG_BOUND_STOP")) a.ctl.cg_bound_stop = atoi(e);
-    a.ctl.chunk_pf = 0;
-    if (const char *e = getenv("NNQP_CHUNK_PF")) a.ctl.chunk_pf = atoi(e);
     if (const char *e = getenv("NNQP_GP_MAX")) a.ctl.gp_max = atoi(e);
     if (const char *e = getenv("NNQP_ETA1")) a.ctl.eta1 = atof(e);
     if (const char *e = getenv("NNQP_ETA2")) a.ctl.eta2 = atof(e);

@@ -411,25 +411,6 @@ struct Rows {
         for (int64_t i = r0 + (int64_t)threadIdx.x * W; i < r1; i += (int64_t)blockDim.x * W)
             f(i, r1 - i < W ? (int)(r1 - i) : W);
     }
-    // The same with an L2 prefetch, dist iterations ahead, of the NP arrays
-    // the pass reads (esize bytes per entry): a warp's chunk of 32 W entries
-    // spans 32 W esize / 128 lines, one lane per line and array.
-    template <int W, int NP, class F>
-    __device__ __forceinline__ void each_chunk_pf(const void *const (&pf)[NP], int esize, int dist, F &&f) const {
-        const int64_t r0 = s0 * 32, r1 = s1 * 32 < n ? s1 * 32 : n;
-        const int lane = threadIdx.x & 31;
-        const int lines = (32 * W * esize) >> 7;
-        const int64_t ahead = (int64_t)dist * blockDim.x * W;
-        for (int64_t i = r0 + (int64_t)threadIdx.x * W; i < r1; i += (int64_t)blockDim.x * W) {
-            if (dist > 0 && lane < NP * lines) {
-                const int64_t wb = i - (int64_t)lane * W + ahead;   // first row of the warp's chunk, ahead
-                const int j = lane / lines, l = lane - j * lines;
-                const int64_t row = wb + (int64_t)l * (128 / esize);
-                if (row < r1) asm volatile("prefetch.global.L2 [%0];" ::"l"((const char *)pf[j] + row * esize));
-            }
-            f(i, r1 - i < W ? (int)(r1 - i) : W);
-        }
-    }
     // The same pass with an L2 prefetch of the warp's next slice of the NP
     // vectors it reads (esize bytes per entry), issued by one lane per
     // 128-byte line: on large systems a warp then has the next rows' loads in

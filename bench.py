@@ -159,11 +159,10 @@ class Steady3dOracle:
     oracle/record_oracle_runs.py (a full oracle run; its active-set polish,
     a few percent of the run, is left out, in the oracle's favour)."""
 
-    def __init__(self, n, threads):
+    def __init__(self, n, threads, runs_dir=None):
         from oracle import oracle as O
         self.O, self.n, self.threads = O, n, threads
-        rec = os.path.join(ROOT, "oracle", "runs", "steady3d_n%d.json" % n)
-        self.record = json.load(open(rec)) if os.path.exists(rec) else None
+        self.record, self.extrapolated = oracle_iterations(n, runs_dir or os.path.join(ROOT, "oracle", "runs"))
         spec = I.config3_steady_3d(n=n)
         t0 = time.perf_counter()
         coords, conn = O.mesh_structured(3, spec.nx)
@@ -187,10 +186,38 @@ class Steady3dOracle:
     def describe(self, k):
         if self.record is None:
             return "no record of the oracle's iteration count for steady3d_n%d" % self.n
+        how = (self.extrapolated or "recorded full oracle run, kkt %.1e" % self.record["kkt_rel"])
         return ("oracle (FP64 C, MPRGP, %d threads) on the %d^3 steady system: its own assembly + elimination "
                 "timed once (%.1f s), %d MPRGP iterations from the zero start timed, whole solve = setup + "
-                "%d iterations (recorded full oracle run, kkt %.1e; polish excluded)"
-                % (self.threads, self.n, self.t_setup, k, self.record["mprgp_iters"], self.record["kkt_rel"]))
+                "%d iterations (%s; polish excluded)"
+                % (self.threads, self.n, self.t_setup, k, self.record["mprgp_iters"], how))
+
+
+def oracle_iterations(n, runs_dir):
+    """MPRGP iterations of the oracle's full solve of the n^3 steady system:
+    the record of a full oracle run (oracle/record_oracle_runs.py) when there
+    is one; otherwise extrapolated from the records of smaller grids by a
+    least-squares power law iterations = a n^b (at least two records), which
+    the returned note says.  Returns (record or None, note or None)."""
+    import glob
+    import re
+    rec = os.path.join(runs_dir, "steady3d_n%d.json" % n)
+    if os.path.exists(rec):
+        return json.load(open(rec)), None
+    pts = []
+    for f in glob.glob(os.path.join(runs_dir, "steady3d_n*.json")):
+        m = re.match(r"steady3d_n(\d+)\.json$", os.path.basename(f))
+        if m and int(m.group(1)) < n:
+            pts.append((int(m.group(1)), json.load(open(f))["mprgp_iters"]))
+    if len(pts) < 2:
+        return None, None
+    ln = np.log([p[0] for p in pts])
+    li = np.log([p[1] for p in pts])
+    b, a = np.polyfit(ln, li, 1)
+    iters = int(round(math.exp(a + b * math.log(n))))
+    note = ("iteration count extrapolated from recorded full oracle runs at n = %s by iterations = a n^%.2f"
+            % (", ".join(str(p[0]) for p in sorted(pts)), b))
+    return {"mprgp_iters": iters, "kkt_rel": float("nan")}, note
 
 
 def oracle_sample(workload, budget_s=20.0, n=None, lumped=False):

@@ -194,3 +194,21 @@ def test_replica_timing_path_world_size_2(tmp_path):
     assert all(p.returncode == 0 for p in procs), [o[1][-500:] for o in outs]
     assert all(r["max"] == 11.0 for r in res)
     assert sum(r["units"] for r in res) == 6
+
+
+def test_oracle_iteration_count_record_or_power_law(tmp_path):
+    """The oracle sample of the benchmark scales a timed batch of MPRGP
+    iterations by the iteration count of a recorded full oracle run; without
+    a record for the grid it extrapolates the records of smaller grids by a
+    power law and says so."""
+    import json
+    sys.path.insert(0, ROOT)
+    import bench
+    for n, it in ((40, 20000), (80, 40000)):
+        (tmp_path / ("steady3d_n%d.json" % n)).write_text(json.dumps({"mprgp_iters": it, "kkt_rel": 1e-14}))
+    rec, note = bench.oracle_iterations(40, str(tmp_path))
+    assert rec["mprgp_iters"] == 20000 and note is None
+    rec, note = bench.oracle_iterations(160, str(tmp_path))
+    assert rec["mprgp_iters"] == 80000 and "extrapolated" in note and "n = 40, 80" in note
+    rec, note = bench.oracle_iterations(30, str(tmp_path))
+    assert rec is None

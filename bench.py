@@ -28,17 +28,17 @@ Options: --precision fp64|mixed|both (default both for steady3d),
 shrink the grid, --e2e-steps (end-to-end repeats, default 5).
 
 Other workloads (--workload), each printing its own line:
-  transient3d  config 2: 40^3 x 6 tets, dt = 0.01, 50 backward-Euler steps
+  transient3d  40^3 x 6 tets, dt = 0.01, 50 backward-Euler steps
                (one warm-started QP per step) in one launch; --mass
                consistent|lumped; a step = assembly + the 50-step run
-  steady2d     config 1 (50 x 50, 2D); a step = assembly + one solve
-  batch        config 4 (512 2D instances, one persistent launch); a step =
+  steady2d     2D 50 x 50 square, rotated tensor; a step = assembly + one solve
+  batch        512 2D instances of 21^2 - 201^2 nodes in one persistent launch; a step =
                one batched solve of all instances, --precision fp64|mixed;
                also reports the single-system FP64 solver on the same instances
   cube_hole    the cube with a cubic hole (Sec. 5.1 analogue; --m, --mesh
                kuhn|mirrored); a step = assembly + one solve; also reports the
                Galerkin solution's departure from [0, 1] (an unbounded solve)
-  serve        config 5 (Poisson arrivals, request r seeded (2015, r));
+  serve        Poisson arrivals at 200/s for 60 s, request r seeded (2015, r);
                reports p50/p99 latency
 """
 from __future__ import annotations
@@ -824,7 +824,7 @@ def main():
         line["vs_plain_fp64"] = m["value"] / line["value"]
         line["precision_note"] = "the line is the plain FP64 solve; \"mixed\" is the same workload in mixed precision"
     if args.workload == "steady3d" and not args.no_serving and not args.n:
-        # the serving stream (config 5) on the same GPU, reported beside the line
+        # the serving stream (Poisson arrivals) on the same GPU, reported beside the line
         args.cur_precision = args.serve_precision
         line["serving"] = serving_object(run_serve(P, torch, args, rank), args)
     if rank == 0 and not args.no_cpu_baseline:

@@ -150,6 +150,7 @@ static nn_status run_batch(int count, nn_system *const *systems, double *const *
     ctl.mu = 1e-4;
     ctl.cg_variant = 0;
     ctl.cg_bound_stop = 0;
+    ctl.keep_p = 0;
     if (const char *e = getenv("NNQP_BATCH_CG_VARIANT")) ctl.cg_variant = atoi(e);
     if (const char *e = getenv("NNQP_CG_BOUND_STOP")) ctl.cg_bound_stop = atoi(e);
     if (const char *e = getenv("NNQP_GP_MAX")) ctl.gp_max = atoi(e);

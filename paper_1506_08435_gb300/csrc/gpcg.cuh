@@ -220,6 +220,8 @@ struct GpcgCtl {
                          // 1: Chronopoulos-Gear PCG (2 barriers, one fused reduction);
                          // 2: pipelined PCG (1 barrier: product, updates and
                          //    reduction in one pass; needs GpcgVecs::m2)
+    int keep_p;          // 1: the packed direction pass stores p with an L2 evict-last policy
+                         //    (the product gathers it next, while its operator streams past)
     int cg_bound_stop;   // 1: end the CG phase as soon as x + s leaves the box;
                          // 0: run CG to its stall test, the projected search clips
 };
@@ -635,6 +637,7 @@ __device__ int gpcg_solve(Team &T, const Rows &R, const Op &A, const Bounds<V> &
                     const void *pf2[2] = {v.z, v.p};
                     if (aligned16(pf2)) {
                         constexpr int W = Pack<V>::W;
+                        const uint64_t keep = l2_evict_last_policy();
                         R.each_chunk<W>([&](int64_t i, int cnt) {
                             if (cnt < W) {
                                 for (int j = 0; j < cnt; ++j) v.p[i + j] = v.z[i + j] + vb * v.p[i + j];
@@ -645,7 +648,10 @@ __device__ int gpcg_solve(Team &T, const Rows &R, const Op &A, const Bounds<V> &
                             ld_pack(v.p + i, pv);
 #pragma unroll
                             for (int j = 0; j < W; ++j) pv[j] = zv[j] + vb * pv[j];
-                            st_pack(v.p + i, pv);
+                            if (C.keep_p)
+                                st_pack_keep(v.p + i, pv, keep);
+                            else
+                                st_pack(v.p + i, pv);
                         });
                     } else {
                         R.each_pf(pf2, (int)sizeof(V), pf_on, [&](int64_t i) { v.p[i] = v.z[i] + vb * v.p[i]; });

@@ -464,6 +464,24 @@ __device__ __forceinline__ void st_pack(V *p, const V (&o)[Pack<V>::W]) {
     *reinterpret_cast<typename Pack<V>::T *>(p) = t;
 }
 
+// st_pack with an L2 evict-last policy: for vectors that the next pass
+// reads again (the search direction the product gathers), so that the
+// operator streaming past with evict-first loads does not push them out.
+__device__ __forceinline__ void st_pack_keep(float *p, const float (&o)[4], uint64_t pol) {
+    asm volatile("st.global.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(p), "f"(o[0]), "f"(o[1]),
+                 "f"(o[2]), "f"(o[3]), "l"(pol)
+                 : "memory");
+}
+__device__ __forceinline__ void st_pack_keep(double *p, const double (&o)[2], uint64_t pol) {
+    asm volatile("st.global.L2::cache_hint.v2.f64 [%0], {%1, %2}, %3;" ::"l"(p), "d"(o[0]), "d"(o[1]), "l"(pol)
+                 : "memory");
+}
+__device__ __forceinline__ uint64_t l2_evict_last_policy() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
 // True if every pointer is 16-byte aligned (the packed passes need it; the
 // rows of a block start at a multiple of 32).
 template <int K>

@@ -936,9 +936,14 @@ def result_line(r, args, prec, dist, ws, hbm_peak, peak_src):
         line["alu"] = {"bound": "alu", "pipe": "fp64", "achieved": ach, "peak": FP64_PIPE_PEAK_GFLOPS,
                        "unit": "GFLOP/s", "frac": ach / FP64_PIPE_PEAK_GFLOPS, "flops_per_launch": fl64,
                        "peak_source": "152 SMs x 2 DFMA/clk (ncu unit count) x 2 flop x 2.07 GHz"}
+        hbm_frac = roof.get("dram_frac") or roof["frac"]
         if line["alu"]["frac"] > max(roof["frac"], roof.get("dram_frac") or 0.0):
             roof["bound"] = "alu"
             roof["bound_note"] = "the FP64 pipe fraction (alu) exceeds the HBM fraction"
+        elif line["alu"]["frac"] >= 0.8 * hbm_frac:
+            roof["bound_note"] = ("co-bound: the FP64 pipe fraction (alu %.2f, algorithmic FP64 operations) is close "
+                                  "to the HBM fraction (%.2f, %s)"
+                                  % (line["alu"]["frac"], hbm_frac, "DRAM" if roof.get("dram_frac") else "algorithmic"))
     for key in ("graph", "dmp", "sequential_fp64"):
         if r.get(key):
             line["galerkin_dmp" if key == "dmp" else key] = r[key]

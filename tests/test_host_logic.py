@@ -212,3 +212,28 @@ def test_oracle_iteration_count_record_or_power_law(tmp_path):
     assert rec["mprgp_iters"] == 80000 and "extrapolated" in note and "n = 40, 80" in note
     rec, note = bench.oracle_iterations(30, str(tmp_path))
     assert rec is None
+
+
+def test_result_line_carries_the_contract_keys_and_names_the_bound():
+    """The JSON line built from one timed run: the contract's keys, the
+    roofline with algorithmic and DRAM figures, the FP64 pipe as a second
+    roof, and the e2e object."""
+    sys.path.insert(0, ROOT)
+    import argparse
+    import bench
+    infos = [dict(spmv=100, spmv64=100, cg_iters=90, iterations=3, refinements=0, fp64_fallback=0, kkt_rel=1e-11,
+                  status=0, flops64_algo=8.0e11, flops_algo=8.0e11)]
+    r = dict(times=[1000.0], infos=infos, kern_ms=[990.0], kern_bytes=[5.0e12], units_per_step=1, e2e=[1010.0],
+             h2d=123, d2h=45, clocks={"sm_mhz": 2070.0}, launches=3, nnz_free=None, config={"workload": "w"},
+             dtype="f64", unit="QP solves/s", metric="QP solves/s")
+    args = argparse.Namespace(steps=1, warmup=3)
+    line = bench.result_line(r, args, "fp64", None, 1, 6795.5, "measured")
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling",
+              "vs_baseline", "dtype", "data", "config", "roofline", "gpu_launches", "clocks", "e2e"):
+        assert k in line, k
+    assert abs(line["value"] - 1.0) < 1e-12 and line["e2e"]["h2d_bytes_per_step"] == 123
+    roof = line["roofline"]
+    assert roof["unit"] == "GB/s" and abs(roof["achieved"] - 5.0e12 / 0.99 / 1e9) < 1e-6
+    assert roof["traffic"] is None and "no ncu summary" in roof["traffic_source"]
+    assert line["alu"]["bound"] == "alu" and 0.6 < line["alu"]["frac"] < 0.7
+    assert roof["bound"] == "hbm" and "co-bound" in roof["bound_note"]

@@ -30,6 +30,14 @@ What each function follows:
 * ``kkt``              -- first-order optimality measure of the box QP.
 * ``transient``        -- backward Euler, one warm-started QP per step
   (Sec. 2.2.2 and Algorithm 1).
+* ``dsatur``           -- the colouring that orders the unknowns of the SSOR
+  preconditioner: Brelaz's saturation-degree greedy rule (Comm. ACM 22,
+  1979), ties by larger degree, then smaller index.
+* ``ssor_apply``       -- z = M^-1 r for the symmetric SOR matrix
+  M = (D + w L) D^-1 (D + w U) / (w (2 - w)) of A_FF with the unknowns
+  ordered by (colour, index) (the paper's CG uses block Jacobi/ILU(0),
+  Sec. 5 and 5.1; SSOR is the multicolour triangular-sweep counterpart):
+  two sparse triangular solves on the permuted matrix.
 
 Every function here is pinned by ``tests/test_oracle_pins.py`` against
 closed forms, textbook special cases, brute force or invariants.
@@ -360,3 +368,57 @@ def transient(red: Reduced, c0_full, lo, hi, nsteps, rtol=1e-12, threads=1):
 
 def objective(A, b, x):
     return 0.5 * x @ (A @ x) - b @ x
+
+
+# --------------------------------------------------------------------------
+# SSOR preconditioner
+# --------------------------------------------------------------------------
+
+def dsatur(A):
+    """Colour of each vertex of the graph of A's pattern (diagonal ignored):
+    repeatedly the uncoloured vertex with the most distinct colours among its
+    neighbours takes the smallest colour none of them has; ties go to the
+    vertex with more neighbours, then to the smaller index."""
+    import heapq
+    A = sp.csr_matrix(A)
+    n = A.shape[0]
+    nbrs = [[int(j) for j in A.indices[A.indptr[i]:A.indptr[i + 1]] if j != i] for i in range(n)]
+    color = [-1] * n
+    sat = [set() for _ in range(n)]
+    heap = [(0, -len(nbrs[i]), i) for i in range(n)]
+    heapq.heapify(heap)
+    while heap:
+        s_neg, d_neg, v = heapq.heappop(heap)
+        if color[v] >= 0 or -s_neg != len(sat[v]):
+            continue                      # coloured, or an older entry of v
+        c = 0
+        while c in sat[v]:
+            c += 1
+        color[v] = c
+        for j in nbrs[v]:
+            if color[j] < 0 and c not in sat[j]:
+                sat[j].add(c)
+                heapq.heappush(heap, (-len(sat[j]), -len(nbrs[j]), j))
+    return np.array(color, np.int32)
+
+
+def ssor_apply(A, color, r, omega=1.0, face=None):
+    """z = M_F^-1 r_F on the face F (all unknowns if face is None; z = 0
+    outside F), M the SSOR matrix of A_FF with the unknowns of F ordered by
+    (colour, index): y = (D + w L)^-1 r, then z = w (2 - w) (D + w U)^-1 D y."""
+    import scipy.sparse.linalg as spl
+    A = sp.csr_matrix(A)
+    n = A.shape[0]
+    F = np.arange(n) if face is None else np.flatnonzero(np.asarray(face) != 0)
+    z = np.zeros(n)
+    if len(F) == 0:
+        return z
+    order = F[np.lexsort((F, np.asarray(color)[F]))]
+    Ap = A[order][:, order].tocsr()
+    D = sp.diags(Ap.diagonal())
+    L = sp.tril(Ap, k=-1)
+    U = sp.triu(Ap, k=1)
+    y = spl.spsolve_triangular((D + omega * L).tocsr(), np.asarray(r, np.float64)[order], lower=True)
+    zp = spl.spsolve_triangular((D + omega * U).tocsr(), D @ y, lower=False)
+    z[order] = omega * (2.0 - omega) * zp
+    return z

@@ -370,13 +370,22 @@ def solver_code(P, args):
     return {"gpcg": P.NN_SOLVER_GPCG, "lbfgs": P.NN_SOLVER_LBFGS, "tron": P.NN_SOLVER_TRON}[args.solver]
 
 
+def precond_opts(P, args):
+    """preconditioner fields of nn_solve_opts"""
+    return dict(precond=P.NN_PC_SSOR if args.precond == "ssor" else P.NN_PC_JACOBI, ssor_omega=args.omega)
+
+
+def precond_name(args):
+    return "ssor(omega %g)" % args.omega if getattr(args, "precond", "jacobi") == "ssor" else "jacobi"
+
+
 def transient_config(spec, args):
     """config of the default workload (both arms print the same one)."""
     return {"workload": "transient3d_n40_dt0.01_50steps", "nodes": spec.n_nodes, "tets": spec.n_elems,
             "qp_per_step": spec.nsteps, "rtol": args.rtol, "l2": "flushed between steps (256 MB write)",
             "solver": args.solver + ("(ksp %g)" % args.ksp_rtol if args.solver == "tron" else ""),
             "precision": getattr(args, "cur_precision", args.precision), "mass": args.mass,
-            "first_iterate": "projected 3c^n - 3c^(n-1) + c^(n-2)"}
+            "first_iterate": "projected 3c^n - 3c^(n-1) + c^(n-2)", "precond": precond_name(args)}
 
 
 def run_transient(P, torch, args, rank):
@@ -386,7 +395,7 @@ def run_transient(P, torch, args, rank):
     prob = P.Problem(spec, device=dev)
     mixed = args.cur_precision == "mixed"
     opts = P.solve_opts(rtol=args.rtol, solver=solver_code(P, args), ksp_rtol=args.ksp_rtol,
-                        precision=P.NN_PREC_MIXED if mixed else P.NN_PREC_FP64)
+                        precision=P.NN_PREC_MIXED if mixed else P.NN_PREC_FP64, **precond_opts(P, args))
     aopts = P.assemble_opts(build_mixed=1 if mixed else 0, lumped_mass=1 if args.mass == "lumped" else 0)
     c0 = torch.tensor(spec.c0, device=dev)
     cf = torch.zeros_like(c0)
@@ -441,7 +450,7 @@ def run_steady(P, torch, args, rank, dim):
     dev = torch.device("cuda")
     prec = {"mixed": P.NN_PREC_MIXED, "auto": P.NN_PREC_AUTO}.get(args.cur_precision, P.NN_PREC_FP64)
     opts = P.solve_opts(rtol=args.rtol, precision=prec, max_iter=args.max_iter,
-                        solver=solver_code(P, args), ksp_rtol=args.ksp_rtol)
+                        solver=solver_code(P, args), ksp_rtol=args.ksp_rtol, **precond_opts(P, args))
     aopts = P.assemble_opts(build_mixed=1 if prec != P.NN_PREC_FP64 else 0)
     prob = P.Problem(spec, device=dev)
     c = torch.zeros(spec.n_nodes, dtype=torch.float64, device=dev)
@@ -540,7 +549,8 @@ def run_steady(P, torch, args, rank, dim):
                         {"workload": name, "nodes": spec.n_nodes, "free": desc.get("n_free"),
                          "rtol": args.rtol,
                          "solver": args.solver + ("(ksp %g)" % args.ksp_rtol if args.solver == "tron" else ""),
-                         "precision": args.cur_precision, "l2": "flushed between steps (256 MB write)"}),
+                         "precision": args.cur_precision, "precond": precond_name(args),
+                         "l2": "flushed between steps (256 MB write)"}),
                 dtype="f64" if prec == P.NN_PREC_FP64 else "f32+f64", unit="QP solves/s", metric="QP solves/s")
 
 
@@ -755,6 +765,9 @@ def main():
                     help="capacity matrix of the transient workload")
     ap.add_argument("--solver", default="gpcg", choices=["gpcg", "lbfgs", "tron"])
     ap.add_argument("--ksp-rtol", type=float, default=1e-1, help="TRON: subspace tolerance relative to the face gradient at the Cauchy point")
+    ap.add_argument("--precond", default="jacobi", choices=["jacobi", "ssor"],
+                    help="preconditioner of the CG iterations (ssor: multicolour SSOR, FP64 only)")
+    ap.add_argument("--omega", type=float, default=1.0, help="SSOR relaxation factor")
     ap.add_argument("--n", type=int, default=0)
     ap.add_argument("--m", type=int, default=16, help="cube with a hole: n = 9m hexahedra per side")
     ap.add_argument("--mesh", default="mirrored", choices=["kuhn", "mirrored"], help="cube with a hole: mesh type")
@@ -785,8 +798,8 @@ def main():
         args.precision = "both"
     elif args.precision == "default":
         args.precision = "fp64"
-    if args.precision == "both" and args.workload != "steady3d":
-        args.precision = "fp64"
+    if args.precision == "both" and (args.workload != "steady3d" or args.precond == "ssor"):
+        args.precision = "fp64"   # (the SSOR preconditioner runs in FP64)
 
     if args.impl == "reference":
         return reference_arm(args, rank)
@@ -853,7 +866,8 @@ def steady3d_config(spec, n, args):
     return {"workload": "steady3d_n%d" % n, "nodes": int(spec.n_nodes), "tets": 6 * n ** 3,
             "free": int((np.asarray(spec.dmask) == 0).sum()), "rtol": args.rtol,
             "solver": args.solver + ("(ksp %g)" % args.ksp_rtol if args.solver == "tron" else ""),
-            "precision": args.precision, "l2": "inputs far larger than L2, flushed between steps (256 MB write)"}
+            "precision": args.precision, "precond": precond_name(args),
+            "l2": "inputs far larger than L2, flushed between steps (256 MB write)"}
 
 
 def reference_arm(args, rank):
@@ -904,8 +918,12 @@ def result_line(r, args, prec, dist, ws, hbm_peak, peak_src):
     # kernel sources as they are now (counters of an older kernel are void)
     infos = r["infos"]
     spl = sum(i["spmv"] for i in infos) / args.steps
+    # (a solver other than GPCG, or the SSOR preconditioner, runs other code:
+    # its summary carries the solver and preconditioner in the name)
+    tag = prec + ("" if getattr(args, "solver", "gpcg") == "gpcg" else "_" + args.solver) + \
+        ("_ssor" if getattr(args, "precond", "jacobi") == "ssor" else "")
     traffic, traffic_src = profile_traffic(os.path.join(ROOT, "profiles"), r.get("kernel_name", "k_solve_grid"),
-                                           r["config"]["workload"], prec, source_digest(),
+                                           r["config"]["workload"], tag, source_digest(),
                                            r.get("profile_scale_from"), spl, r.get("nnz_free"))
     roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
             "traffic": traffic, "traffic_source": traffic_src,
@@ -927,6 +945,9 @@ def result_line(r, args, prec, dist, ws, hbm_peak, peak_src):
             "phases_per_step": sum(i["iterations"] for i in infos) / args.steps,
             "refinements_per_step": sum(i["refinements"] for i in infos) / args.steps,
             "fp64_fallbacks": int(sum(i["fp64_fallback"] for i in infos))}
+    pcs = sum(i.get("pc_applies", 0) for i in infos)
+    if pcs:
+        line["pc_applies_per_step"] = pcs / args.steps
     # the FP64 pipe as the second roof: algorithmic FP64 operations of the
     # launch / its time, against 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
     fl64 = sum(i.get("flops64_algo", 0.0) for i in infos) / args.steps

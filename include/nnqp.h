@@ -63,6 +63,7 @@ enum { NN_COEF_TENSOR = 0, NN_COEF_VELOCITY = 1 };
 enum { NN_SOLVER_GPCG = 0, NN_SOLVER_LBFGS = 1, NN_SOLVER_TRON = 2 };
 enum { NN_PREC_FP64 = 0, NN_PREC_MIXED = 1, NN_PREC_AUTO = 2 };
 enum { NN_FMT_SELL = 0, NN_FMT_CSR = 1 };
+enum { NN_PC_JACOBI = 0, NN_PC_SSOR = 1 };
 
 /* Last error message of the calling thread ("" if none). */
 const char *nn_last_error(void);
@@ -160,6 +161,7 @@ typedef struct {
     int64_t sell_slices, sell_stored; /* SELL-32 slices and stored off-diagonal slots */
     double lo, hi, dt;
     size_t device_bytes;            /* device memory held by the system */
+    int ssor_colors;                /* colours of the SSOR ordering (0 before nn_precond_setup) */
 } nn_system_desc;
 
 nn_status nn_system_describe(const nn_system *s, nn_system_desc *d);
@@ -167,7 +169,8 @@ nn_status nn_system_describe(const nn_system *s, nn_system_desc *d);
 /* Copies one internal array into a caller buffer (for verification):
  *   0 K rowptr int64[N+1], 1 K col int32[nnz], 2 K val f64[nnz], 3 M val f64[nnz],
  *   4 F f64[N], 5 free->node int32[NF], 6 A rowptr int64[NF+1], 7 A col int32[nnzF],
- *   8 A val f64[nnzF], 9 b0 f64[NF], 10 coords f64[N*dim], 11 conn int32[E*(dim+1)].
+ *   8 A val f64[nnzF], 9 b0 f64[NF], 10 coords f64[N*dim], 11 conn int32[E*(dim+1)],
+ *   12 colour of each free unknown in the SSOR ordering int32[NF] (after nn_precond_setup).
  * Full-node arrays (0-4) need keep_full.  bytes must equal the array size.
  * Synchronizes the stream.  Errors: INVALID_ARG. */
 nn_status nn_system_copy_out(const nn_system *s, int what, void *dst, size_t bytes, int dst_memory, void *stream);
@@ -200,6 +203,18 @@ typedef struct {
     double ksp_rtol;     /* TRON: the subspace steps of an iteration stop once the free-face
                             gradient is at most ksp_rtol times its value at the Cauchy point
                             (default 1e-1; the paper's TRON1/2/3 use 1e-1, 1e-2, 1e-3) */
+    int precond;         /* preconditioner of the CG iterations (GPCG's CG phases, TRON's subspace
+                            steps) on the current face F: NN_PC_JACOBI (default), z = D^-1 r, or
+                            NN_PC_SSOR, z = M_F^-1 r with the multicolour symmetric SOR matrix
+                            M = (D + omega L) D^-1 (D + omega U) / (omega (2 - omega)) of A_FF
+                            (see nn_precond_apply).  The paper preconditions its CG with block
+                            Jacobi/ILU(0) (Sec. 5, Sec. 5.1); SSOR is the triangular-sweep
+                            preconditioner that a colouring makes parallel.  SSOR runs with
+                            precision FP64 (AUTO is taken as FP64), the SELL format and the GPCG
+                            or TRON solver; other combinations are INVALID_ARG.  The first solve
+                            with SSOR builds the ordering (nn_precond_setup) if it is not built */
+    double ssor_omega;   /* relaxation factor of NN_PC_SSOR, 0 < omega < 2 (default 1: symmetric
+                            Gauss-Seidel) */
 } nn_solve_opts;
 
 void nn_solve_opts_default(nn_solve_opts *o);
@@ -222,6 +237,8 @@ typedef struct {
     double flops64_algo;   /* algorithmic FP64 operations: 2 nnz per FP64 product plus the
                               arithmetic of the fused vector passes */
     double flops_algo;     /* the same over all precisions */
+    int64_t pc_applies;    /* SSOR preconditioner applications (0 with Jacobi); bytes_algo and the
+                              flop counts include them */
 } nn_solve_info;
 
 /* Solves the steady QP  min 1/2 x'Ax - x'b0, lo <= x <= hi  over the free
@@ -322,6 +339,51 @@ nn_status nn_spmv(const nn_system *s, const double *x, double *y, int format, in
  *   - Launches two kernels on `stream`; no cudaMalloc, cudaFree or other
  *     allocating call.  Asynchronous. */
 nn_status nn_spmv_mixed_noalloc(const nn_system *s, const double *x, double *y, void *stream);
+
+/* ---------------------------------------------------- SSOR preconditioning
+ * Symmetric SOR as the preconditioner of the CG iterations.  The paper's CG
+ * runs with block Jacobi/ILU(0) (Sec. 5, Sec. 5.1; TRON1/2/3 use it too):
+ * triangular sweeps over the unknowns in order.  Sweeps are sequential along
+ * the ordering; with the unknowns ordered colour by colour (no two coupled
+ * unknowns share a colour), each colour's rows depend only on other colours,
+ * so a sweep is one parallel pass per colour.  With A_FF = D + L + U in that
+ * ordering (L strictly lower), the preconditioner is
+ *     M = (D + omega L) D^-1 (D + omega U) / (omega (2 - omega)),
+ * symmetric positive definite for 0 < omega < 2 (omega = 1: symmetric
+ * Gauss-Seidel), and z = M^-1 r is one forward and one backward SOR sweep
+ * from z = 0. */
+
+/* Greedy colouring by saturation degree (DSatur, Brelaz, Comm. ACM 22, 1979)
+ * of the graph of an n x n pattern (host arrays rowptr int64 [n+1], col int32
+ * [nnz]; diagonal entries ignored, the pattern must be symmetric): repeatedly
+ * the uncoloured vertex with the most distinct colours among its neighbours
+ * (ties: the larger degree, then the smaller index) takes the smallest colour
+ * none of its neighbours has.  color int32 [n] receives the colours 0..k-1,
+ * *ncolors = k.  On the structured meshes it finds 4 colours in 3D (the Kuhn
+ * stencil's least number) and 3 in 2D.  Host only.  Errors: INVALID_ARG (bad
+ * pattern, more than 64 colours). */
+nn_status nn_color_dsatur(int64_t n, const int64_t *rowptr, const int32_t *col, int32_t *color, int *ncolors);
+
+/* Builds the SSOR ordering of the system once: nn_color_dsatur of A's free
+ * pattern, then the rows of each colour in ascending order, stored as
+ * SELL-32 slices of their lower (earlier colour) and upper (later colour)
+ * entries.  The device arrays (about the bytes of A's SELL operator) belong to
+ * the system (nn_system_describe counts them).  No-op if already built.
+ * The build changes the system: do not run it (or a first SSOR solve, which
+ * calls it) while another call uses the same system.  Synchronizes the
+ * stream.  Errors: OOM, CUDA, INVALID_ARG. */
+nn_status nn_precond_setup(nn_system *s, void *stream);
+
+/* z = P r for the preconditioner `precond` (NN_PC_JACOBI: P = D_F^-1;
+ * NN_PC_SSOR: P = M_F^-1 above, relaxation omega) restricted to the face
+ * F = {i : face[i] != 0} (face device uint8 [NF], or NULL for all free
+ * unknowns); z_i = 0 outside F.  r, z device double [NF], distinct.  Runs
+ * the solve kernels' sweep code in a launch of its own, so the tests can
+ * compare it entry by entry with a plain implementation.  Builds the SSOR
+ * ordering if needed.  Synchronizes the stream.  Errors: INVALID_ARG (unknown
+ * precond, omega outside (0, 2), NULL vectors), TIMEOUT. */
+nn_status nn_precond_apply(nn_system *s, int precond, double omega, const uint8_t *face, const double *r, double *z,
+                           void *stream);
 
 /* ------------------------------------------------------- row sharding
  * One QP spread over several ranks (one GPU each), as the paper scales one

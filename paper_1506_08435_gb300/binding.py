@@ -37,9 +37,10 @@ NN_COEF_TENSOR, NN_COEF_VELOCITY = 0, 1
 NN_SOLVER_GPCG, NN_SOLVER_LBFGS, NN_SOLVER_TRON = 0, 1, 2
 NN_PREC_FP64, NN_PREC_MIXED, NN_PREC_AUTO = 0, 1, 2
 NN_FMT_SELL, NN_FMT_CSR = 0, 1
+NN_PC_JACOBI, NN_PC_SSOR = 0, 1
 
 COPY = dict(K_rowptr=0, K_col=1, K_val=2, M_val=3, F=4, free_node=5, A_rowptr=6, A_col=7, A_val=8, b0=9,
-            coords=10, conn=11)
+            coords=10, conn=11, ssor_color=12)
 
 
 class NnError(RuntimeError):
@@ -63,13 +64,15 @@ class nn_assemble_opts(ctypes.Structure):
 class nn_system_desc(ctypes.Structure):
     _fields_ = [("dim", c_int), ("n_nodes", c_int64), ("n_elems", c_int64), ("n_free", c_int64),
                 ("nnz_full", c_int64), ("nnz_free", c_int64), ("sell_slices", c_int64), ("sell_stored", c_int64),
-                ("lo", c_double), ("hi", c_double), ("dt", c_double), ("device_bytes", c_size_t)]
+                ("lo", c_double), ("hi", c_double), ("dt", c_double), ("device_bytes", c_size_t),
+                ("ssor_colors", c_int)]
 
 
 class nn_solve_opts(ctypes.Structure):
     _fields_ = [("solver", c_int), ("precision", c_int), ("format", c_int), ("rtol", c_double),
                 ("max_iter", c_int64), ("lbfgs_m", c_int), ("grid_blocks", c_int), ("wait_timeout_s", c_double),
-                ("inner_rtol", c_double), ("extrapolate", c_int), ("ksp_rtol", c_double)]
+                ("inner_rtol", c_double), ("extrapolate", c_int), ("ksp_rtol", c_double), ("precond", c_int),
+                ("ssor_omega", c_double)]
 
 
 class nn_solve_info(ctypes.Structure):
@@ -77,7 +80,7 @@ class nn_solve_info(ctypes.Structure):
                 ("cg_iters", c_int64), ("refinements", c_int64), ("kkt_rel", c_double), ("kkt_inf", c_double),
                 ("objective", c_double), ("time_ms", c_double), ("bytes_algo", c_double),
                 ("active_lo", c_int64), ("active_hi", c_int64), ("fp64_fallback", c_int64),
-                ("flops64_algo", c_double), ("flops_algo", c_double)]
+                ("flops64_algo", c_double), ("flops_algo", c_double), ("pc_applies", c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -111,7 +114,8 @@ EXPORTS = ["nn_last_error", "nn_version", "nn_kernel_launches", "nn_device_alloc
            "nn_batch_solve", "nn_batch_autotune", "nn_serve_opts_default", "nn_serve_create",
            "nn_serve_submit", "nn_serve_poll", "nn_serve_drain", "nn_serve_stats", "nn_serve_destroy",
            "nn_plan_create", "nn_plan_launch", "nn_plan_result", "nn_plan_destroy",
-           "nn_shard_plan", "nn_shard_build", "nn_shard_spmv"]
+           "nn_shard_plan", "nn_shard_build", "nn_shard_spmv",
+           "nn_color_dsatur", "nn_precond_setup", "nn_precond_apply"]
 
 _lib = None
 
@@ -169,6 +173,9 @@ def lib():
     L.nn_shard_plan.argtypes = [c_int64, vp, vp, c_int, c_int, POINTER(nn_shard_desc)]
     L.nn_shard_build.argtypes = [c_int64, vp, vp, c_int, c_int, vp, vp, vp, vp, vp, vp]
     L.nn_shard_spmv.argtypes = [c_int64, vp, vp, vp, vp, vp, vp]
+    L.nn_color_dsatur.argtypes = [c_int64, vp, vp, vp, POINTER(c_int)]
+    L.nn_precond_setup.argtypes = [vp, vp]
+    L.nn_precond_apply.argtypes = [vp, c_int, c_double, vp, vp, vp, vp]
     _lib = L
     return L
 
@@ -539,3 +546,29 @@ def nn_shard_spmv(nrows, local_rowptr, local_col, val, x_ext, y, stream=None):
     _check(lib().nn_shard_spmv(nrows, _ptr(local_rowptr)[0], _ptr(local_col)[0], _ptr(val)[0], _ptr(x_ext)[0],
                                _ptr(y)[0], _stream(stream)))
     return y
+
+
+# ---------------------------------------------------------------- SSOR preconditioning
+
+def nn_color_dsatur(rowptr, col):
+    """DSatur colouring of the graph of a symmetric CSR pattern (numpy int64
+    rowptr, int32 col, host): (colour int32 [n], number of colours)."""
+    rowptr = np.ascontiguousarray(rowptr, np.int64)
+    col = np.ascontiguousarray(col, np.int32)
+    n = len(rowptr) - 1
+    color = np.zeros(max(n, 1), np.int32)
+    k = c_int()
+    _check(lib().nn_color_dsatur(n, rowptr.ctypes.data, col.ctypes.data, color.ctypes.data, byref(k)))
+    return color[:n], k.value
+
+
+def nn_precond_setup(sys, stream=None):
+    _check(lib().nn_precond_setup(sys.handle, _stream(stream)))
+
+
+def nn_precond_apply(sys, r, z, precond=NN_PC_SSOR, omega=1.0, face=None, stream=None):
+    """z = P r on the device (torch tensors): the solve kernels' Jacobi or
+    multicolour SSOR preconditioner on the face (uint8 tensor or None)."""
+    _check(lib().nn_precond_apply(sys.handle, precond, omega, _ptr(face)[0] if face is not None else None,
+                                  _ptr(r)[0], _ptr(z)[0], _stream(stream)))
+    return z

@@ -13,7 +13,7 @@ OBJ = os.path.join(HERE, "_build")
 
 SOURCES = ["scan.cu", "assemble.cu", "solve.cu", "solve_grid_steady.cu", "solve_grid_transient.cu",
            "solve_grid_mixed.cu", "solve_grid_mixed_transient.cu", "solve_grid_tma.cu", "batch.cu", "batch_fp64.cu", "batch_mixed.cu",
-           "serve.cpp", "shard.cpp", "capi.cpp"]
+           "precond.cu", "serve.cpp", "shard.cpp", "capi.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

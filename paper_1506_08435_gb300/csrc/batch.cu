@@ -256,6 +256,10 @@ nn_status nn_batch_solve(int count, nn_system *const *systems, double *const *c,
     nn_solve_opts_default(&d);
     if (!o) o = &d;
     NN_TRY(check_opts(o));
+    if (o->precond != NN_PC_JACOBI) {
+        set_error("batched solves use the Jacobi preconditioner");
+        return NN_ERR_INVALID_ARG;
+    }
     if (count < 1 || !systems || !c) {
         set_error("nn_batch_solve: count >= 1 and arrays are required");
         return NN_ERR_INVALID_ARG;
@@ -281,6 +285,10 @@ nn_status nn_batch_autotune(int count, nn_system *const *systems, const nn_solve
     nn_solve_opts_default(&d);
     if (!o) o = &d;
     NN_TRY(check_opts(o));
+    if (o->precond != NN_PC_JACOBI) {
+        set_error("batched solves use the Jacobi preconditioner");
+        return NN_ERR_INVALID_ARG;
+    }
     if (count < 1 || !systems) {
         set_error("nn_batch_autotune: count >= 1 and systems are required");
         return NN_ERR_INVALID_ARG;

@@ -101,6 +101,20 @@ nn_status check_opts(const nn_solve_opts *o) {
                   "0 < inner_rtol < 1, 0 <= extrapolate <= 2, 0 < ksp_rtol < 1)");
         return NN_ERR_INVALID_ARG;
     }
+    if (o->precond != NN_PC_JACOBI && o->precond != NN_PC_SSOR) {
+        set_error("unknown preconditioner %d", o->precond);
+        return NN_ERR_INVALID_ARG;
+    }
+    if (o->precond == NN_PC_SSOR) {
+        if (!(o->ssor_omega > 0.0 && o->ssor_omega < 2.0)) {
+            set_error("SSOR needs 0 < omega < 2 (got %g)", o->ssor_omega);
+            return NN_ERR_INVALID_ARG;
+        }
+        if (o->precision == NN_PREC_MIXED || o->format != NN_FMT_SELL || o->solver == NN_SOLVER_LBFGS) {
+            set_error("the SSOR preconditioner runs in FP64 (or AUTO) on the SELL format with GPCG or TRON");
+            return NN_ERR_INVALID_ARG;
+        }
+    }
     return NN_OK;
 }
 
@@ -187,6 +201,7 @@ nn_status nn_system_describe(const nn_system *s, nn_system_desc *d) {
     d->hi = s->hi;
     d->dt = s->dt;
     d->device_bytes = s->arena.bytes;
+    d->ssor_colors = s->ssor.ncolors;
     return NN_OK;
 }
 
@@ -211,6 +226,24 @@ nn_status nn_system_copy_out(const nn_system *s, int what, void *dst, size_t byt
         case 9: src = s->b0; need = sizeof(double) * s->NF; break;
         case 10: src = s->coords; need = sizeof(double) * s->N * s->dim; break;
         case 11: src = s->conn; need = sizeof(int32_t) * s->E * (s->dim + 1); break;
+        case 12: {   // host array
+            if (s->ssor_color.empty()) {
+                set_error("nn_system_copy_out: the SSOR ordering is not built (nn_precond_setup)");
+                return NN_ERR_INVALID_ARG;
+            }
+            need = sizeof(int32_t) * s->NF;
+            if (bytes != need) {
+                set_error("nn_system_copy_out: array 12 has %zu bytes, buffer has %zu", need, bytes);
+                return NN_ERR_INVALID_ARG;
+            }
+            if (dst_memory == NN_MEM_DEVICE) {
+                NN_CUDA_TRY(cudaMemcpyAsync(dst, s->ssor_color.data(), need, cudaMemcpyHostToDevice, S(stream)));
+                NN_CUDA_TRY(cudaStreamSynchronize(S(stream)));
+            } else {
+                std::memcpy(dst, s->ssor_color.data(), need);
+            }
+            return NN_OK;
+        }
         default: set_error("nn_system_copy_out: unknown array %d", what); return NN_ERR_INVALID_ARG;
     }
     if (!src) {
@@ -240,6 +273,8 @@ void nn_solve_opts_default(nn_solve_opts *o) {
     o->inner_rtol = 1e-4;
     o->extrapolate = 2;
     o->ksp_rtol = 1e-1;
+    o->precond = NN_PC_JACOBI;
+    o->ssor_omega = 1.0;
 }
 
 static nn_status solve_common(nn_system *s, const nn_solve_opts *o, int want_transient, int nsteps,

@@ -8,8 +8,8 @@
 //     backtracking until the Armijo condition q(w) - q(x) <= mu g'(w - x)
 //     holds; repeated until the active set stops changing or the decrease
 //     stalls (eta1);
-//   * CG phase: Jacobi-preconditioned CG on the face {l < x < h} with the
-//     active entries frozen, run until the face residual is small or the
+//   * CG phase: preconditioned CG on the face {l < x < h} (Jacobi, or the
+//     multicolour SSOR of ssor.cuh with CGV = 3) with the active entries frozen, run until the face residual is small or the
 //     decrease per iteration stalls (eta2); then a projected search along the
 //     CG step, which clips entries that crossed a bound.  If every active
 //     entry is binding (its projected gradient is zero) the next phase is CG
@@ -30,6 +30,7 @@
 #include <stdint.h>
 #include "team.cuh"
 #include "ops.cuh"
+#include "ssor.cuh"
 
 namespace nnqp {
 
@@ -206,6 +207,7 @@ struct GpcgVecs {
     const V *dinv;
     uint8_t *fm;          // face mask of the current CG phase (1 = free)
     V *m2;                // second product input of the pipelined CG (variant 2)
+    const SsorF64 *pc;    // SSOR ordering of the textbook form with CGV = 3 (else unused)
 };
 
 struct GpcgCtl {
@@ -232,18 +234,22 @@ struct GpcgCtl {
 // algorithmic operations spmv * 2 nnz + fl * n.
 struct GpcgStats {
     int64_t spmv = 0, cg = 0, phases = 0, vec = 0, fl = 0;
+    int64_t pc = 0;   // SSOR applications (their traffic is counted apart from vec)
     double gp2 = 0.0;
 };
 
 // Runs GPCG from the iterate in v.x (projected first).  On exit v.x holds
 // the final iterate, v.g its gradient (pointers may have been swapped).
 // CGV >= 0 fixes the CG variant at compile time (one body per kernel);
-// CGV = -1 reads it from C.cg_variant.
+// CGV = -1 reads it from C.cg_variant; CGV = 3 is the textbook form with the
+// multicolour SSOR preconditioner of v.pc in place of Jacobi (FP64 only).
 template <class Team, class Op, typename V, int CGV = -1>
 __device__ int gpcg_solve(Team &T, const Rows &R, const Op &A, const Bounds<V> &B, GpcgVecs<V> &v,
                           const GpcgCtl &C, GpcgStats &st) {
     const double tol2 = C.tol * C.tol, ftol2 = C.face_tol * C.face_tol;
     const V zero = (V)0, one = (V)1;
+    constexpr bool PC = CGV == 3;
+    static_assert(!PC || sizeof(V) == 8, "the SSOR preconditioner runs in FP64");
     const bool pf_on = op_streams(A);   // large system: vector passes prefetch
     R.each([&](int64_t i) { v.x[i] = clampv(v.x[i], B.l(i), B.h(i)); });
     st.vec += 2;
@@ -526,24 +532,45 @@ __device__ int gpcg_solve(Team &T, const Rows &R, const Op &A, const Bounds<V> &
                     mn = t;
                 }
             } else {
-                // textbook preconditioned CG
+                // textbook preconditioned CG (z = D^-1 r, or z = M_F^-1 r by
+                // the SSOR sweeps when PC)
                 Acc<V> a3[1];
                 double d3[1];
-                R.each([&](int64_t i) {
-                    V xi = v.x[i];
-                    const bool fr = xi > B.l(i) && xi < B.h(i);
-                    v.fm[i] = fr ? 1 : 0;
-                    V ri = fr ? -v.g[i] : zero;
-                    V zi = v.dinv[i] * ri;
-                    v.r[i] = ri;
-                    v.z[i] = zi;
-                    v.p[i] = zi;
-                    v.s[i] = zero;
-                    a3[0] += ri * zi;
-                });
+                if constexpr (PC) {
+                    R.each([&](int64_t i) {
+                        V xi = v.x[i];
+                        const bool fr = xi > B.l(i) && xi < B.h(i);
+                        v.fm[i] = fr ? 1 : 0;
+                        v.r[i] = fr ? -v.g[i] : zero;
+                        v.s[i] = zero;
+                    });
+                    st.vec += 5;
+                    if (!T.sync()) return ST_TIMEOUT;
+                    if (!ssor_apply(T, *v.pc, v.fm, v.dinv, v.r, v.w, v.z, [&](int64_t i, double zi) {
+                            v.p[i] = zi;
+                            a3[0] += v.r[i] * zi;
+                        }))
+                        return ST_TIMEOUT;
+                    ++st.pc;
+                    st.vec += 2;
+                    st.fl += 2;
+                } else {
+                    R.each([&](int64_t i) {
+                        V xi = v.x[i];
+                        const bool fr = xi > B.l(i) && xi < B.h(i);
+                        v.fm[i] = fr ? 1 : 0;
+                        V ri = fr ? -v.g[i] : zero;
+                        V zi = v.dinv[i] * ri;
+                        v.r[i] = ri;
+                        v.z[i] = zi;
+                        v.p[i] = zi;
+                        v.s[i] = zero;
+                        a3[0] += ri * zi;
+                    });
+                    st.vec += 8;
+                    st.fl += 3;
+                }
                 if (!team_sum(T, a3, d3)) return ST_TIMEOUT;
-                st.vec += 8;
-                st.fl += 3;
                 double rho = d3[0];
                 if (!(rho > 0.0)) break;
                 double maxdec = 0.0;
@@ -586,7 +613,29 @@ __device__ int gpcg_solve(Team &T, const Rows &R, const Op &A, const Bounds<V> &
                         }
                     };
                     const void *al6[6] = {v.s, v.p, v.r, v.q, v.dinv, v.z};
-                    if (!count_cross && aligned16(al6)) {
+                    if constexpr (PC) {
+                        // s and r only: z comes from the sweeps below
+                        const void *pf4[4] = {v.s, v.p, v.r, v.q};
+                        R.each_pf(pf4, (int)sizeof(V), pf_on, [&](int64_t i) {
+                            V si = v.s[i] + va * v.p[i];
+                            V ri = v.r[i] - va * v.q[i];
+                            v.s[i] = si;
+                            v.r[i] = ri;
+                            a5[1] += ri * ri;
+                            if (count_cross) {
+                                V xs = v.x[i] + si;
+                                a5[2] += (xs < B.l(i) || xs > B.h(i)) ? one : zero;
+                            }
+                        });
+                        if (!T.sync()) return ST_TIMEOUT;
+                        if (!ssor_apply(T, *v.pc, v.fm, v.dinv, v.r, v.w, v.z,
+                                        [&](int64_t i, double zi) { a5[0] += v.r[i] * zi; }))
+                            return ST_TIMEOUT;
+                        ++st.pc;
+                        st.vec -= 2;   // no D^-1 read, no z write in the update pass
+                        st.vec += 1;   // r read again by the dot product of the sweep
+                        st.fl -= 1;
+                    } else if (!count_cross && aligned16(al6)) {
                         constexpr int W = Pack<V>::W;
                         R.each_chunk<W>([&](int64_t i, int cnt) {
                             if (cnt < W) {

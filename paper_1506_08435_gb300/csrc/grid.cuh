@@ -76,6 +76,7 @@ struct GridArgs {
     uint8_t *fmask;         // [n] face mask of the CG phases
     int tma_slot_entries;   // FMT 3: 32 x the widest slice (slot size of the streamed operator)
     int tma_slots;          // FMT 3: slots per warp
+    SsorF64 pc;             // SSOR ordering and omega (CG form 3, TRON with ncolors > 0)
 };
 
 // Initial iterate of a backward-Euler step: linear extrapolation of the last
@@ -212,7 +213,7 @@ __global__ void __launch_bounds__(TPB, TPB >= 512 ? 1 : mode_min_blocks(MODE)) k
             transient_predict<GridTeam>(R, a, x, step);   // own rows; the solve's first pass syncs
         }
         if (!(den > 0.0)) den = a.den_fallback;
-        if (mode_mixed(MODE)) {
+        if constexpr (mode_mixed(MODE)) {
             GpcgVecs<float> v{a.v32[0], a.v32[1], a.v32[2], a.v32[3], a.v32[4], a.v32[5],
                               a.v32[6], a.v32[7], a.v32[8], a.v32[9], a.dinv32, a.fmask, a.v32[12]};
             GpcgVecs<double> v64{x, a.v64[1], a.v64[2], a.v64[3], a.v64[4], a.v64[5],
@@ -245,6 +246,8 @@ __global__ void __launch_bounds__(TPB, TPB >= 512 ? 1 : mode_min_blocks(MODE)) k
         } else {
             GpcgVecs<double> v{x, a.v64[1], a.v64[2], a.v64[3], a.v64[4], a.v64[5],
                                a.v64[6], a.v64[7], a.v64[8], b, a.dinv64, a.fmask, a.v64[10]};
+            const SsorF64 pcv = a.pc;
+            if constexpr (CGV == 3) v.pc = &pcv;
             GpcgCtl c = a.ctl;
             c.tol = a.rtol * den;
             c.face_tol = 0.5 * c.tol;
@@ -268,6 +271,7 @@ __global__ void __launch_bounds__(TPB, TPB >= 512 ? 1 : mode_min_blocks(MODE)) k
             cnt[3] = gs.cg;
             cnt[4] = gs.phases;
             cnt[6] = gs.vec;
+            cnt[10] = gs.pc;
             cnt[12] += gs.fl;
             gp2 = gs.gp2;
         }
@@ -283,8 +287,9 @@ constexpr int FMT_SELL_SMEM = 2;
 constexpr int FMT_SELL_TMA = 3;
 
 // Kernel of one mode for format fmt (NN_FMT_SELL / NN_FMT_CSR /
-// FMT_SELL_SMEM), CG variant cgv (0, 1, 2) and threads per block tpb (256,
-// 512); nullptr if that combination is not built.
+// FMT_SELL_SMEM), CG variant cgv (0, 1, 2; 3 = textbook CG with the SSOR
+// preconditioner, FP64 modes) and threads per block tpb (256, 512, 768);
+// nullptr if that combination is not built.
 GridKernel grid_kernel_steady(int fmt, int cgv, int tpb);
 GridKernel grid_kernel_transient(int fmt, int cgv, int tpb);
 GridKernel grid_kernel_mixed(int fmt, int cgv, int tpb);

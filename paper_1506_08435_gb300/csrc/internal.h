@@ -31,9 +31,10 @@ void count_launch();
     } while (0)
 
 // SELL-32 storage of the off-diagonal part of a square matrix: slice s holds
-// rows [32s, 32s+32); its width w_s = max off-diagonal count of those rows;
-// entry k of row 32s+l is at sptr[s] + 32k + l (column-major in the slice).
-// Padding slots carry the row's own column and value 0.
+// rows [32s, 32s+32); its width w_s = max off-diagonal count of those rows,
+// rounded up to even; entry k of row 32s+l is at
+// sptr[s] + 64 (k/2) + 2l + (k%2) (pairs of entries interleaved by row,
+// sell_idx in ops.cuh).  Padding slots carry the row's own column and value 0.
 template <typename T>
 struct SellMat {
     int64_t n = 0;
@@ -42,6 +43,26 @@ struct SellMat {
     int64_t *sptr = nullptr;     // [nslices+1], shared between value copies
     int32_t *col = nullptr;      // [stored],    shared between value copies
     T *val = nullptr;            // [stored]
+};
+
+// Device view of the multicolour SSOR ordering of A = Kt_FF (nn_precond_setup).
+// The rows of colour c fill slices cslice[c] .. cslice[c+1]-1 of 32 rows each,
+// rows ascending; lane l of slice s is free unknown row[32s + l] (-1 = padding
+// lane).  Entry k of that lane's lower part (columns of earlier colours) is at
+// lptr[s] + 32k + l, of its upper part (later colours) at uptr[s] + 32k + l;
+// slices are as wide as their longest row, the padding entries carry value 0
+// and a column that the sweep has already written in that pass (the first row
+// of colour 0 for lower parts, of the last colour for upper parts).
+struct SsorF64 {
+    int ncolors;
+    bool stream;             // parts far larger than L2: evict-first loads
+    double omega;
+    const int64_t *cslice;   // [ncolors + 1]
+    const int32_t *row;      // [32 * slices]
+    const int64_t *lptr;     // [slices + 1]
+    const int64_t *uptr;     // [slices + 1]
+    const int32_t *lcol, *ucol;
+    const double *lval, *uval;
 };
 
 // Device allocations owned by one object, released together.
@@ -113,7 +134,30 @@ struct nn_system {
     double *mdiag64 = nullptr;      // [NF]
     double *b0 = nullptr;           // [NF] F_F - K_FD c_D
     size_t assembly_peak_bytes = 0; // device bytes held at the end of assembly (system + temporaries)
+    nnqp::SsorF64 ssor{};           // SSOR ordering (ncolors = 0 until nn_precond_setup)
+    int64_t ssor_slices = 0;
+    std::vector<int32_t> ssor_color; // colour of each free unknown (host)
     double anorm_inf = 0;           // ||A||_inf
     double b0norm = 0;              // ||b0||_2
     bool has_csr = false, has_mixed = false, has_full = false;
 };
+
+namespace nnqp {
+// Host arrays of the SSOR ordering (the device view SsorF64 points at copies).
+struct SsorHost {
+    int ncolors = 0;
+    std::vector<int32_t> color;                 // [n]
+    std::vector<int64_t> cslice, lptr, uptr;    // [ncolors+1], [slices+1], [slices+1]
+    std::vector<int32_t> row, lcol, ucol;
+    std::vector<double> lval, uval;
+};
+// The ordering of the n x n matrix whose off-diagonals are held in
+// pair-interleaved SELL-32 (ns slices, host copies of sptr / col / val).
+nn_status ssor_layout(int64_t n, int64_t ns, const int64_t *sptr, const int32_t *scol, const double *sval,
+                      SsorHost &h);
+// Builds the SSOR ordering of s once (nn_precond_setup); synchronizes st.
+nn_status ssor_setup(nn_system *s, cudaStream_t st);
+// DSatur colouring of a symmetric pattern (nn_color_dsatur), without the
+// argument checks.
+nn_status dsatur_color(int64_t n, const int64_t *rowptr, const int32_t *col, int32_t *color, int *ncolors);
+}  // namespace nnqp

@@ -244,8 +244,8 @@ nn_status nn_serve_create(size_t hbm_budget_bytes, const nn_serve_opts *o, nn_se
     if (!o) o = &d;
     NN_TRY(check_opts(&o->solve));
     if (o->max_inflight < 1 || o->max_inflight > 64 || o->queue_capacity < 1 ||
-        o->solve.solver != NN_SOLVER_GPCG || o->solve.format != NN_FMT_SELL) {
-        set_error("nn_serve_create: 1 <= max_inflight <= 64, queue_capacity >= 1, GPCG on SELL");
+        o->solve.solver != NN_SOLVER_GPCG || o->solve.format != NN_FMT_SELL || o->solve.precond != NN_PC_JACOBI) {
+        set_error("nn_serve_create: 1 <= max_inflight <= 64, queue_capacity >= 1, GPCG on SELL with Jacobi");
         return NN_ERR_INVALID_ARG;
     }
     nn_server *h = new nn_server();
@@ -293,8 +293,8 @@ nn_status nn_serve_submit(nn_server *h, const nn_problem *p, const nn_solve_opts
     }
     if (!o) o = &sv->opts.solve;
     NN_TRY(check_opts(o));
-    if (o->solver != NN_SOLVER_GPCG || o->format != NN_FMT_SELL) {
-        set_error("nn_serve_submit: served requests are solved by GPCG on the SELL format");
+    if (o->solver != NN_SOLVER_GPCG || o->format != NN_FMT_SELL || o->precond != NN_PC_JACOBI) {
+        set_error("nn_serve_submit: served requests are solved by Jacobi-preconditioned GPCG on the SELL format");
         return NN_ERR_INVALID_ARG;
     }
     auto r = std::make_shared<Request>();

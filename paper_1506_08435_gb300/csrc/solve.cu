@@ -72,8 +72,9 @@ __global__ void __launch_bounds__(kSolveThreads, 2) k_tron_grid(GridArgs a) {
             cnt[12] += 4;
         }
         if (!(den > 0.0)) den = a.den_fallback;
+        const SsorF64 pcv = a.pc;
         TronVecs v{x0, a.v64[1], a.v64[7], a.v64[8], a.v64[2], a.v64[3], a.v64[4], a.v64[5], a.v64[6],
-                   a.v64[10], b, a.dinv64, a.fmask};
+                   a.v64[10], b, a.dinv64, a.fmask, a.pc.ncolors > 0 ? &pcv : nullptr};
         const TronCtl c{a.rtol * den, 0.5 * a.rtol * den, a.ksp_rtol, a.ctl.max_spmv, 50};
         TronStats ts;
         const int status = tron_solve(T, R, a.A, B, v, c, ts);
@@ -87,6 +88,7 @@ __global__ void __launch_bounds__(kSolveThreads, 2) k_tron_grid(GridArgs a) {
         cnt[3] = ts.cg;
         cnt[4] = ts.iters;
         cnt[6] = ts.vec;
+        cnt[10] = ts.pc;
         cnt[12] += ts.fl;
         if (!step_outputs(T, R, a, x0, step, nsteps, status, cnt, ts.gp2, den)) return;
     }
@@ -254,7 +256,17 @@ struct Scratch {
 
 }  // namespace
 
-void fill_info(const nn_system *s, const int64_t *cnt, const double *sc, int precision, nn_solve_info *info) {
+// algorithmic bytes of one SSOR application (ssor.cuh): every off-diagonal
+// entry once (value + column), the row ids of both sweeps, and per row the
+// forward sweep's r, 1/a_ii, face byte, y written and y gathered, the
+// backward sweep's y, 1/a_ii, face byte, z written and z gathered
+double bytes_ssor(int64_t nnz, int64_t n) { return 12.0 * (double)(nnz - n) + 74.0 * (double)n; }
+
+// its operations: a multiply-add per off-diagonal entry, 7 per row
+double flops_ssor(int64_t nnz, int64_t n) { return 2.0 * (double)(nnz - n) + 7.0 * (double)n; }
+
+void fill_info(const nn_system *s, const int64_t *cnt, const double *sc, int precision, int precond,
+               nn_solve_info *info) {
     std::memset(info, 0, sizeof(*info));
     info->status = (int)cnt[0];
     info->spmv64 = cnt[1];
@@ -265,13 +277,16 @@ void fill_info(const nn_system *s, const int64_t *cnt, const double *sc, int pre
     info->active_lo = cnt[8];
     info->active_hi = cnt[9];
     info->fp64_fallback = cnt[11];
-    info->flops64_algo = 2.0 * cnt[1] * (double)s->nnzF + (double)cnt[12] * s->NF;
+    info->pc_applies = precond == NN_PC_SSOR ? cnt[10] : 0;   // (slot 10 holds L-BFGS resets otherwise)
+    info->flops64_algo = 2.0 * cnt[1] * (double)s->nnzF + (double)cnt[12] * s->NF +
+                         (double)info->pc_applies * flops_ssor(s->nnzF, s->NF);
     info->flops_algo = info->flops64_algo + 2.0 * cnt[2] * (double)s->nnzF + (double)cnt[13] * s->NF;
     info->kkt_rel = std::sqrt(sc[0]) / sc[1];
     info->kkt_inf = NAN;
     info->objective = NAN;
     info->bytes_algo = cnt[1] * bytes_spmv(s->nnzF, s->NF, 8, 8) + cnt[2] * bytes_spmv(s->nnzF, s->NF, 4, 4) +
-                       (double)cnt[6] * 8.0 * s->NF + (double)cnt[7] * 4.0 * s->NF;
+                       (double)cnt[6] * 8.0 * s->NF + (double)cnt[7] * 4.0 * s->NF +
+                       (double)info->pc_applies * bytes_ssor(s->nnzF, s->NF);
     (void)precision;
 }
 
@@ -313,6 +328,12 @@ nn_status plan_build(nn_system *s, const nn_solve_opts *o, int mode, int nsteps,
         set_error("CSR format is available in FP64 only");
         return NN_ERR_INVALID_ARG;
     }
+    const bool ssor = o->precond == NN_PC_SSOR;
+    if (ssor && (mixed || fmt != NN_FMT_SELL || o->solver == NN_SOLVER_LBFGS)) {
+        set_error("the SSOR preconditioner runs in FP64 on the SELL format with GPCG or TRON");
+        return NN_ERR_INVALID_ARG;
+    }
+    if (ssor) NN_TRY(ssor_setup(s, st));
     P.s = s;
     P.o = *o;
     P.mode = mode;
@@ -366,6 +387,12 @@ nn_status plan_build(nn_system *s, const nn_solve_opts *o, int mode, int nsteps,
     a.ctl.cg_bound_stop = 0;
     if (const char *e = getenv("NNQP_CG_VARIANT")) a.ctl.cg_variant = atoi(e);
     if (const char *e = getenv("NNQP_CG_BOUND_STOP")) a.ctl.cg_bound_stop = atoi(e);
+    if (ssor) {
+        // the textbook CG form with the SSOR sweeps in place of D^-1
+        a.pc = s->ssor;
+        a.pc.omega = o->ssor_omega;
+        if (o->solver == NN_SOLVER_GPCG) a.ctl.cg_variant = 3;
+    }
     // the search direction stays in L2 for the product that gathers it
     // (measured on the 150^3 solve: FP64 182.9 -> 176.7 us per product,
     // mixed 107.9 -> 106.5 us; no effect where the vectors fit L2 anyway)
@@ -418,7 +445,8 @@ nn_status plan_build(nn_system *s, const nn_solve_opts *o, int mode, int nsteps,
     const bool large = !driver && (slices > (int64_t)4 * 8 * sms || force_large);
     if (!driver && slices <= (int64_t)4 * 8 * sms && slices > (int64_t)8 * sms / 2) tpb = 512;
     if (!driver && (force_tpb == 256 || force_tpb == 512)) tpb = force_tpb;
-    if (large && a.ctl.cg_variant == 0 && fmt == NN_FMT_SELL && force_tpb != 512) tpb = kLargeThreads;
+    if (large && (a.ctl.cg_variant == 0 || a.ctl.cg_variant == 3) && fmt == NN_FMT_SELL && force_tpb != 512)
+        tpb = kLargeThreads;
     if (force_large) {
         a.A.stream = true;
         a.A32.stream = true;
@@ -606,7 +634,8 @@ nn_status plan_collect(GridPlan &P, cudaStream_t st, float ms, nn_solve_info *in
     nn_status worst = NN_OK;
     for (int k = 0; k < nsteps; ++k) {
         nn_solve_info inf;
-        fill_info(P.s, &cnt[(size_t)k * kCounters], &sc[(size_t)k * kScalars], mode_mixed(P.mode), &inf);
+        fill_info(P.s, &cnt[(size_t)k * kCounters], &sc[(size_t)k * kScalars], mode_mixed(P.mode), P.o.precond,
+                  &inf);
         if (k == 0) inf.time_ms = ms;
         if (infos && k < ninfos) infos[k] = inf;
         if (inf.status != NN_OK && worst == NN_OK) worst = (nn_status)inf.status;
@@ -829,7 +858,8 @@ nn_status solve_entry(nn_system *s, const nn_solve_opts *o, int mode, int nsteps
 bool auto_mixed(const nn_system *s) { return s->has_mixed && (double)s->nnzF * 8.0 > kStreamBytes; }
 
 int mode_for(const nn_system *s, const nn_solve_opts *o) {
-    const bool mixed = o->precision == NN_PREC_MIXED || (o->precision == NN_PREC_AUTO && auto_mixed(s));
+    const bool mixed = o->precision == NN_PREC_MIXED ||
+                       (o->precision == NN_PREC_AUTO && o->precond != NN_PC_SSOR && auto_mixed(s));
     if (s->dt > 0.0) return mixed ? MODE_MIXED_TR : MODE_TRANSIENT;
     return mixed ? MODE_MIXED : MODE_STEADY;
 }

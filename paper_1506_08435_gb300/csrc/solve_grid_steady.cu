@@ -20,7 +20,13 @@ GridKernel grid_kernel_steady(int fmt, int cgv, int tpb) {
             default: return nullptr;
         }
     }
-    if (tpb == 768) return cgv == 0 ? k_solve_grid<0, MODE_STEADY, 0, 768> : nullptr;
+    if (tpb == 768) {
+        switch (cgv) {
+            case 0: return k_solve_grid<0, MODE_STEADY, 0, 768>;
+            case 3: return k_solve_grid<0, MODE_STEADY, 3, 768>;
+            default: return nullptr;
+        }
+    }
     if (tpb == 512) {
         switch (cgv) {
             case 1: return k_solve_grid<0, MODE_STEADY, 1, 512>;
@@ -33,6 +39,7 @@ GridKernel grid_kernel_steady(int fmt, int cgv, int tpb) {
         case 0: return k_solve_grid<0, MODE_STEADY, 0, 256>;
         case 1: return k_solve_grid<0, MODE_STEADY, 1, 256>;
         case 2: return k_solve_grid<0, MODE_STEADY, 2, 256>;
+        case 3: return k_solve_grid<0, MODE_STEADY, 3, 256>;
         default: return nullptr;
     }
 }

@@ -25,6 +25,7 @@ GridKernel grid_kernel_transient(int fmt, int cgv, int tpb) {
         case 0: return k_solve_grid<0, MODE_TRANSIENT, 0, 256>;
         case 1: return k_solve_grid<0, MODE_TRANSIENT, 1, 256>;
         case 2: return k_solve_grid<0, MODE_TRANSIENT, 2, 256>;
+        case 3: return k_solve_grid<0, MODE_TRANSIENT, 3, 256>;
         default: return nullptr;
     }
 }

@@ -11,7 +11,8 @@
 //     (x10) while s(alpha) satisfies both the sufficient decrease
 //     q(x+s) - q(x) <= mu0 g's and ||s|| <= mu1 Delta and still changes,
 //     else backtracked (x0.1) until it does;
-//   * subspace steps: Jacobi-preconditioned CG on the face {l < x < h} for
+//   * subspace steps: preconditioned CG (Jacobi, or the multicolour SSOR of
+//     ssor.cuh when v.pc is set) on the face {l < x < h} for
 //     A_FF w = -g_F, truncated where it leaves the trust region ||w|| <=
 //     Delta (Steihaug) and stopped once the face residual is at most
 //     ksp_rtol times the face gradient at the Cauchy point, then a projected
@@ -39,6 +40,7 @@ struct TronCtl {
 
 struct TronStats {
     int64_t spmv = 0, cg = 0, iters = 0, minor = 0, vec = 0, fl = 0;
+    int64_t pc = 0;   // SSOR applications (their traffic is counted apart from vec)
     double gp2 = 0.0;
 };
 
@@ -49,6 +51,7 @@ struct TronVecs {
     double *xo;               // iterate at the start of the outer iteration
     const double *b, *dinv;
     uint8_t *fm;              // face mask of the subspace step (1 = free)
+    const SsorF64 *pc;        // SSOR ordering, or nullptr for Jacobi
 };
 
 constexpr double kTronMu0 = 1e-2;     // sufficient decrease
@@ -173,22 +176,43 @@ __device__ int tron_solve(Team &T, const Rows &R, const Op &A, const Bounds<doub
             if (!(st.gp2 > tol2) || st.spmv >= C.max_spmv) break;
             ++st.minor;
             double a0[2] = {0.0, 0.0}, d0[2];
-            R.each([&](int64_t i) {
-                const double xi = v.x[i];
-                const bool fr = xi > B.l(i) && xi < B.h(i);
-                v.fm[i] = fr ? 1 : 0;
-                const double ri = fr ? -v.g[i] : 0.0;
-                const double zi = v.dinv[i] * ri;
-                v.r[i] = ri;
-                v.z[i] = zi;
-                v.p[i] = zi;
-                v.s[i] = 0.0;
-                a0[0] += ri * zi;
-                a0[1] += ri * ri;
-            });
+            if (v.pc) {
+                R.each([&](int64_t i) {
+                    const double xi = v.x[i];
+                    const bool fr = xi > B.l(i) && xi < B.h(i);
+                    v.fm[i] = fr ? 1 : 0;
+                    const double ri = fr ? -v.g[i] : 0.0;
+                    v.r[i] = ri;
+                    v.s[i] = 0.0;
+                    a0[1] += ri * ri;
+                });
+                if (!T.sync()) return ST_TIMEOUT;
+                if (!ssor_apply(T, *v.pc, v.fm, v.dinv, v.r, v.w, v.z, [&](int64_t i, double zi) {
+                        v.p[i] = zi;
+                        a0[0] += v.r[i] * zi;
+                    }))
+                    return ST_TIMEOUT;
+                ++st.pc;
+                st.vec += 7;
+                st.fl += 4;
+            } else {
+                R.each([&](int64_t i) {
+                    const double xi = v.x[i];
+                    const bool fr = xi > B.l(i) && xi < B.h(i);
+                    v.fm[i] = fr ? 1 : 0;
+                    const double ri = fr ? -v.g[i] : 0.0;
+                    const double zi = v.dinv[i] * ri;
+                    v.r[i] = ri;
+                    v.z[i] = zi;
+                    v.p[i] = zi;
+                    v.s[i] = 0.0;
+                    a0[0] += ri * zi;
+                    a0[1] += ri * ri;
+                });
+                st.vec += 8;
+                st.fl += 5;
+            }
             if (!team_sum(T, a0, d0)) return ST_TIMEOUT;
-            st.vec += 8;
-            st.fl += 5;
             double rz = d0[0];
             if (!(rz > 0.0)) break;                // nothing to do on this face
             if (mi == 0) ktol2 = fmax(C.ksp_rtol * C.ksp_rtol * d0[1], C.face_tol * C.face_tol);
@@ -234,21 +258,39 @@ __device__ int tron_solve(Team &T, const Rows &R, const Op &A, const Bounds<doub
                 }
                 const double al = o1[2];
                 double a2[3] = {0.0, 0.0, 0.0}, d2[3];
-                R.each([&](int64_t i) {
-                    const double si = v.s[i] + al * v.p[i];
-                    const double ri = v.r[i] - al * v.q[i];
-                    const double zi = v.dinv[i] * ri;
-                    v.s[i] = si;
-                    v.r[i] = ri;
-                    v.z[i] = zi;
-                    a2[0] += ri * zi;
-                    a2[1] += ri * ri;
-                    a2[2] += si * si;
-                });
+                if (v.pc) {
+                    R.each([&](int64_t i) {
+                        const double si = v.s[i] + al * v.p[i];
+                        const double ri = v.r[i] - al * v.q[i];
+                        v.s[i] = si;
+                        v.r[i] = ri;
+                        a2[1] += ri * ri;
+                        a2[2] += si * si;
+                    });
+                    if (!T.sync()) return ST_TIMEOUT;
+                    if (!ssor_apply(T, *v.pc, v.fm, v.dinv, v.r, v.w, v.z,
+                                    [&](int64_t i, double zi) { a2[0] += v.r[i] * zi; }))
+                        return ST_TIMEOUT;
+                    ++st.pc;
+                    st.vec += 7;
+                    st.fl += 10;
+                } else {
+                    R.each([&](int64_t i) {
+                        const double si = v.s[i] + al * v.p[i];
+                        const double ri = v.r[i] - al * v.q[i];
+                        const double zi = v.dinv[i] * ri;
+                        v.s[i] = si;
+                        v.r[i] = ri;
+                        v.z[i] = zi;
+                        a2[0] += ri * zi;
+                        a2[1] += ri * ri;
+                        a2[2] += si * si;
+                    });
+                    st.vec += 8;
+                    st.fl += 11;
+                }
                 if (!team_sum(T, a2, d2)) return ST_TIMEOUT;
                 ++st.cg;
-                st.vec += 8;
-                st.fl += 11;
                 ss = d2[2];
                 if (d2[1] <= ktol2 || !(d2[0] > 0.0) || st.spmv >= C.max_spmv) break;
                 const double beta = d2[0] / rz;

@@ -383,6 +383,23 @@ def test_cube_hole_qp_and_galerkin_match_oracle(mesh):
         assert cg.min() >= -1e-12
 
 
+def test_sell_padding_equals_the_pattern_count_on_the_cube_with_a_hole():
+    """The library's SELL-32 storage of A holds the off-diagonals plus the
+    padding of 32-row slices with even widths, computed here from the
+    oracle's matrix: the small padding that leaves no room for sigma-sorting
+    on these meshes (rows near the hole are shorter)."""
+    spec = I.cube_with_hole(4)
+    s = gpu_system(spec)
+    d = s.describe()
+    _, red = oracle_reduced(spec)
+    off = np.diff(red.A.indptr) - 1
+    w = np.zeros(((len(off) + 31) // 32) * 32, np.int64)
+    w[:len(off)] = off
+    w = w.reshape(-1, 32).max(axis=1)
+    assert d["sell_stored"] == 32 * int((w + (w & 1)).sum())
+    assert d["sell_stored"] <= 1.03 * (d["nnz_free"] - d["n_free"])
+
+
 def test_transient_step_api_equals_batched_steps():
     spec = I.config2_transient_3d(n=8, nsteps=3)
     s = gpu_system(spec)

@@ -332,12 +332,16 @@ def timed_steps(torch, step, steps, flush, clk):
 
 # ---------------------------------------------------------------- workloads
 
-def profile_traffic(pdir, kname, workload, precision, digest, scale_from=None, products=None, nnz_free=None):
+def profile_traffic(pdir, kname, workload, precision, digest, scale_from=None, products=None, nnz_free=None,
+                    algo_bytes=None):
     """DRAM bytes per launch of kernel kname on this workload from the committed
     ncu summary <kname>_<workload>_<precision>.md in pdir (its line
     "dram_bytes_per_launch: N"), used only while its "source_digest:" line
     equals digest.  Without a summary for the workload itself, the summary of
-    the smaller case scale_from is scaled by products x nnz_free (its
+    the smaller case scale_from is scaled to this launch by algorithmic bytes
+    (its "algo_bytes_per_launch:" line against algo_bytes: the DRAM traffic
+    per algorithmic byte is taken as a property of the kernel), or, where the
+    summary has no such line, by products x nnz_free (its
     "products_per_launch:" and "nnz_free:" lines).  Returns (bytes or None,
     where the figure came from or why there is none)."""
     tfile = os.path.join(pdir, "%s_%s_%s.md" % (kname, workload, precision))
@@ -351,7 +355,8 @@ def profile_traffic(pdir, kname, workload, precision, digest, scale_from=None, p
     fields = {}
     for line in open(tfile):
         key = line.split(":", 1)[0].strip() if ":" in line else ""
-        if key in ("dram_bytes_per_launch", "source_digest", "products_per_launch", "nnz_free"):
+        if key in ("dram_bytes_per_launch", "source_digest", "products_per_launch", "nnz_free",
+                   "algo_bytes_per_launch"):
             v = line.split(":", 1)[1].strip()
             fields[key] = v.split()[0] if v else ""
     if fields.get("source_digest") != digest:
@@ -360,6 +365,9 @@ def profile_traffic(pdir, kname, workload, precision, digest, scale_from=None, p
         traffic = float(fields["dram_bytes_per_launch"])
         if not scaled:
             return traffic, "ncu capture, %s" % name
+        if algo_bytes and fields.get("algo_bytes_per_launch"):
+            traffic *= algo_bytes / float(fields["algo_bytes_per_launch"])
+            return traffic, "ncu capture of a smaller case (%s), scaled by algorithmic bytes" % name
         traffic *= products / float(fields["products_per_launch"]) * nnz_free / float(fields["nnz_free"])
         return traffic, "ncu capture of a smaller case (%s), scaled by products x nnz_free" % name
     except (KeyError, ValueError, TypeError, ZeroDivisionError):
@@ -924,7 +932,7 @@ def result_line(r, args, prec, dist, ws, hbm_peak, peak_src):
         ("_ssor" if getattr(args, "precond", "jacobi") == "ssor" else "")
     traffic, traffic_src = profile_traffic(os.path.join(ROOT, "profiles"), r.get("kernel_name", "k_solve_grid"),
                                            r["config"]["workload"], tag, source_digest(),
-                                           r.get("profile_scale_from"), spl, r.get("nnz_free"))
+                                           r.get("profile_scale_from"), spl, r.get("nnz_free"), kern_bytes)
     roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
             "traffic": traffic, "traffic_source": traffic_src,
             "kernel": "solve kernel (persistent, one launch per step)", "kernel_ms": kern_ms,

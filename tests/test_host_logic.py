@@ -145,8 +145,9 @@ def test_reference_arm_prints_the_contract_line():
 
 def test_profile_traffic_lookup(tmp_path):
     """The bench takes DRAM traffic from a committed ncu summary only while its
-    source digest matches, scales a smaller capture by products x nnz_free,
-    and otherwise reports null with the reason."""
+    source digest matches, scales a smaller capture by algorithmic bytes (or,
+    without them, by products x nnz_free), and otherwise reports null with
+    the reason."""
     sys.path.insert(0, ROOT)
     import bench
     (tmp_path / "k_w_fp64.md").write_text("source_digest: abc\ndram_bytes_per_launch: 1000\n")
@@ -158,6 +159,13 @@ def test_profile_traffic_lookup(tmp_path):
     t, why = bench.profile_traffic(str(tmp_path), "k", "big", "fp64", "abc", "small", 30, 100)
     assert t == 2000.0 * 3 * 2 and "scaled" in why
     assert bench.profile_traffic(str(tmp_path), "k", "other", "fp64", "abc")[0] is None
+    # a summary with its algorithmic bytes scales by the full launch's algorithmic bytes
+    (tmp_path / "k_cap_fp64.md").write_text("source_digest: abc\nproducts_per_launch: 10\nnnz_free: 50\n"
+                                            "algo_bytes_per_launch: 4000\ndram_bytes_per_launch: 2000\n")
+    t, why = bench.profile_traffic(str(tmp_path), "k", "full", "fp64", "abc", "cap", 30, 100, 20000)
+    assert t == 2000.0 * 5 and "algorithmic" in why
+    t, why = bench.profile_traffic(str(tmp_path), "k", "full", "fp64", "abc", "cap", 30, 100)
+    assert t == 2000.0 * 3 * 2 and "products" in why
     (tmp_path / "k_bad_fp64.md").write_text("source_digest: abc\n")
     assert "incomplete" in bench.profile_traffic(str(tmp_path), "k", "bad", "fp64", "abc")[1]
 

@@ -57,3 +57,55 @@ def test_library_colouring_rejects_bad_patterns():
 def test_solve_option_defaults():
     o = P.solve_opts()
     assert o.precond == P.NN_PC_JACOBI and o.ssor_omega == 1.0
+
+
+def _layout_checker(tmp_path):
+    """Builds tests/ssor_layout_check.cpp against the library."""
+    import os
+    import subprocess
+    P.lib()
+    here = os.path.dirname(os.path.abspath(__file__))
+    pkg = os.path.dirname(P.library_path())
+    cuda = os.environ.get("CUDA_HOME", "/usr/local/cuda")
+    exe = str(tmp_path / "ssor_layout_check")
+    subprocess.check_call(["g++", "-O2", "-std=c++17", "-I", os.path.join(pkg, "csrc"), "-I", os.path.join(cuda, "include"),
+                           os.path.join(here, "ssor_layout_check.cpp"), "-o", exe, "-L", pkg, "-lnnqp",
+                           "-Wl,-rpath," + pkg, "-L", os.path.join(cuda, "lib64"), "-lcudart"])
+    return exe
+
+
+@pytest.mark.parametrize("spec,omega,share", [(I.config3_steady_3d(n=16), 1.0, 1.0), (I.config1_steady_2d(n=40), 1.3, 0.7),
+                                              (I.cube_with_hole(3), 0.8, 0.9)], ids=lambda v: getattr(v, "name", str(v)))
+def test_library_ssor_layout_and_sweeps_match_the_oracle(tmp_path, spec, omega, share):
+    """The host half of nn_precond_setup (A's pair-interleaved SELL-32 read
+    back into rows, DSatur, the colour-ordered lower and upper parts) run on
+    the CPU, followed by the two sweeps with the kernels' indexing: equal to
+    the oracle's SSOR application (and no read of an unwritten entry, which
+    the NaN-filled scratch would show)."""
+    import subprocess
+    exe = _layout_checker(tmp_path)
+    _, red = oracle_reduced(spec)
+    A = red.A.tocsr()
+    A.sort_indices()
+    n = A.shape[0]
+    rng = np.random.default_rng(9)
+    r = rng.normal(size=n)
+    face = (rng.uniform(size=n) < share).astype(np.uint8)
+    src, dst = tmp_path / "in.bin", tmp_path / "out.bin"
+    with open(src, "wb") as f:
+        np.array([n, A.nnz], np.int64).tofile(f)
+        A.indptr.astype(np.int64).tofile(f)
+        A.indices.astype(np.int32).tofile(f)
+        A.data.astype(np.float64).tofile(f)
+        r.tofile(f)
+        face.tofile(f)
+        np.array([omega]).tofile(f)
+    subprocess.check_call([exe, str(src), str(dst)])
+    raw = open(dst, "rb").read()
+    z = np.frombuffer(raw[:8 * n], np.float64)
+    col = np.frombuffer(raw[8 * n:], np.int32)
+    ref_col = O.dsatur(A)
+    assert np.array_equal(col, ref_col)
+    ref = O.ssor_apply(A, ref_col, r, omega, face=face)
+    assert np.isfinite(z).all()
+    assert np.abs(z - ref).max() <= 1e-13 * np.abs(ref).max()

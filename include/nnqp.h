@@ -147,7 +147,9 @@ void nn_assemble_opts_default(nn_assemble_opts *o);
  * Host-side validation: dim, sizes, lo <= hi, Dirichlet values in [lo, hi]
  * (INFEASIBLE), NaN in coefficients (NUMERIC).  Device-side validation
  * (status word): connectivity range (INVALID_ARG), zero-measure element
- * (DEGENERATE), non-SPD D_e (NOT_SPD).  Synchronizes the stream.
+ * (DEGENERATE), non-SPD D_e (NOT_SPD); a problem whose every node is a
+ * Dirichlet node has no unknowns and is refused (INVALID_ARG: its solution is
+ * the Dirichlet data).  Synchronizes the stream.
  * On success *out owns all device data; release with nn_system_destroy. */
 nn_status nn_assemble(const nn_problem *p, const nn_assemble_opts *o, void *stream, nn_system **out);
 

@@ -37,15 +37,17 @@ def steady150():
     return spec, red, red.rhs()
 
 
-@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "fp64_ssor"])
 def test_steady_3d_150_kkt_by_oracle(prec, steady150):
     """150^3 x 6 tets (3,442,951 nodes): the GPU solution meets the oracle's
-    KKT test and the bounds exactly."""
+    KKT test and the bounds exactly (plain FP64, mixed precision, and FP64
+    with the multicolour SSOR preconditioner)."""
     spec, red, b = steady150
     s = P.nn_assemble(P.Problem(spec, device=DEV))
     c = torch.zeros(spec.n_nodes, dtype=torch.float64, device=DEV)
     p = P.NN_PREC_MIXED if prec == "mixed" else P.NN_PREC_FP64
-    info = P.nn_qp_solve(s, c, P.solve_opts(precision=p))
+    pc = P.NN_PC_SSOR if prec.endswith("ssor") else P.NN_PC_JACOBI
+    info = P.nn_qp_solve(s, c, P.solve_opts(precision=p, precond=pc))
     assert info["status"] == 0, info
     x = c.cpu().numpy()
     del s

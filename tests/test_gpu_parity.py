@@ -492,6 +492,14 @@ def test_invalid_inputs_are_rejected_and_library_stays_usable():
     assert np.array_equal(c1, c2)
     s, c, info = solve_gpu(base)
     assert info["status"] == 0
+    # every node a Dirichlet node: no unknowns, refused (the solution is the data)
+    empty = I.config1_steady_2d(n=1)
+    assert (empty.dmask == 1).all()
+    with pytest.raises(P.NnError) as e:
+        gpu_system(empty)
+    assert e.value.status == P.NN_ERR_INVALID_ARG
+    s, c, info = solve_gpu(base)
+    assert info["status"] == 0
 
 
 def test_bounded_wait_times_out_with_status(monkeypatch):

@@ -780,6 +780,22 @@ def serving_object(r, args):
             "config": r["config"]}
 
 
+def resolve_precision(args):
+    """--precision default: both precisions for the 150^3 workload (the FP64
+    line with the mixed run as a sub-object), the serving precision for the
+    serving workload, FP64 otherwise; "both" only where the workload has the
+    sub-object and the preconditioner is Jacobi (SSOR runs in FP64)."""
+    if args.workload == "serve" and args.precision == "default":
+        args.precision = args.serve_precision
+    if args.workload == "steady3d" and args.precision == "default":
+        args.precision = "both"
+    elif args.precision == "default":
+        args.precision = "fp64"
+    if args.precision == "both" and (args.workload != "steady3d" or getattr(args, "precond", "jacobi") == "ssor"):
+        args.precision = "fp64"
+    return args
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -789,7 +805,8 @@ def main():
     ap.add_argument("--workload", default="steady3d",
                     choices=["transient3d", "steady3d", "steady2d", "batch", "serve", "cube_hole"])
     ap.add_argument("--precision", default="default", choices=["default", "auto", "fp64", "mixed", "both"],
-                    help="auto: both for steady3d (FP64 line + mixed object), fp64 otherwise")
+                    help="default: both for steady3d (FP64 line + mixed object), the serving precision for serve, "
+                         "fp64 otherwise; auto: the library's NN_PREC_AUTO")
     ap.add_argument("--mass", default="consistent", choices=["consistent", "lumped"],
                     help="capacity matrix of the transient workload")
     ap.add_argument("--solver", default="gpcg", choices=["gpcg", "lbfgs", "tron"])
@@ -821,14 +838,7 @@ def main():
     hbm_peak = pk["hbm_gbs"] if pk else FALLBACK_HBM
     peak_src = "measured (MEASURED_PEAKS.json hbm_gbs)" if pk else "fallback"
 
-    if args.workload == "serve" and args.precision == "default":
-        args.precision = args.serve_precision
-    if args.workload == "steady3d" and args.precision == "default":
-        args.precision = "both"
-    elif args.precision == "default":
-        args.precision = "fp64"
-    if args.precision == "both" and (args.workload != "steady3d" or args.precond == "ssor"):
-        args.precision = "fp64"   # (the SSOR preconditioner runs in FP64)
+    resolve_precision(args)
 
     if args.impl == "reference":
         return reference_arm(args, rank)

@@ -245,3 +245,22 @@ def test_result_line_carries_the_contract_keys_and_names_the_bound():
     assert roof["traffic"] is None and "no ncu summary" in roof["traffic_source"]
     assert line["alu"]["bound"] == "alu" and 0.6 < line["alu"]["frac"] < 0.7
     assert roof["bound"] == "hbm" and "co-bound" in roof["bound_note"]
+
+
+def test_precision_resolution_of_the_bench():
+    sys.path.insert(0, ROOT)
+    import argparse
+    import bench
+
+    def res(**kw):
+        a = dict(workload="steady3d", precision="default", precond="jacobi", serve_precision="auto")
+        a.update(kw)
+        return bench.resolve_precision(argparse.Namespace(**a)).precision
+
+    assert res() == "both"
+    assert res(precond="ssor") == "fp64"
+    assert res(workload="transient3d") == "fp64"
+    assert res(workload="serve") == "auto"
+    assert res(workload="batch", precision="both") == "fp64"
+    assert res(precision="mixed") == "mixed"
+    assert res(precision="auto", workload="steady2d") == "auto"
